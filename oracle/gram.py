@@ -1,0 +1,47 @@
+"""Sufficient statistics (FP64).
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Paper: Section "Notation" defines mat_l[X] (d_l x d_{\\l}) and
+S_l = mat_l[{X}] mat_l[{X}]^T; Section "Algorithm" shows S_l for several
+modalities is the Gram of the column-concatenation of their matricisations.
+Reading (two-axis case): rows of X are cells, so S_cells = X X^T and
+S_genes = X^T X; no 1/n normalisation.
+"""
+
+import numpy as np
+
+
+def log1p_centre(counts: np.ndarray) -> np.ndarray:
+    """Preprocessing used by the scRNA-like workloads: log1p, then centre every
+    column (gene) over the rows (cells).  Returns float64."""
+    x = np.log1p(np.asarray(counts, dtype=np.float64))
+    return x - x.mean(axis=0, keepdims=True)
+
+
+def matricize(t: np.ndarray, axis: int) -> np.ndarray:
+    """mat_l[T]: move ``axis`` to the front and flatten the rest (row-major),
+    giving a d_l x (prod of the other sizes) matrix."""
+    t = np.asarray(t, dtype=np.float64)
+    return np.moveaxis(t, axis, 0).reshape(t.shape[axis], -1)
+
+
+def gram(t: np.ndarray, axis: int) -> np.ndarray:
+    """S_l = mat_l[T] mat_l[T]^T for one tensor (matrix: axis 0 -> X X^T,
+    axis 1 -> X^T X)."""
+    m = matricize(t, axis)
+    return m @ m.T
+
+
+def gram_multimodal(tensors, axis_labels, label) -> np.ndarray:
+    """S_l = sum over modalities containing axis ``label`` of that modality's
+    Gram along it (equivalently the Gram of the concatenated matricisation).
+
+    ``tensors[g]`` has axes named ``axis_labels[g]`` (a tuple of labels)."""
+    s = None
+    for t, labels in zip(tensors, axis_labels):
+        if label not in labels:
+            continue
+        g = gram(t, labels.index(label))
+        s = g if s is None else s + g
+    return s
