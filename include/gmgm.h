@@ -1,0 +1,288 @@
+/*
+ * gmgm.h -- C ABI of the GB300 (sm_103a) implementation of the improved
+ * multi-axis Gaussian graphical model fit ("GmGM", arXiv 2407.19892).
+ *
+ * The model (Introduction; Eq. of Section "The model"): data tensors that
+ * share axes are drawn from a Kronecker-sum-structured (singular) normal,
+ * precision  Psi_1 (+) Psi_2 (+) ... ; one sparse graph Psi_l per axis is the
+ * output.  Algorithm 1 (appendix "The algorithm") fits it in four steps, each
+ * an entry point here:
+ *
+ *   gmgm_gram          S_l = mat_l[D] mat_l[D]^T         (Section "Algorithm")
+ *   gmgm_spectra       top-r eigenpairs of S_l           (Theorem 1; Alg. 1)
+ *   gmgm_lift          singular vectors of the large axis through the small
+ *                      Gram (Section "Algorithm": the eigenvectors of S_l are
+ *                      the singular vectors of mat_l[D])
+ *   gmgm_eigsolve      eigenvalues Lam_l of the MLE      (Proposition on the
+ *                      eigenvalue gradient; existence lemma; Alg. 1 loop)
+ *   gmgm_topk_network  thresh(V_l Lam_l V_l^T) fused     (Alg. 1 last loop;
+ *                      appendix "Computational complexity": threshold while
+ *                      recomposing, O(n_l) memory)
+ *
+ * plus gmgm_preprocess (log1p + column centring of counts, with the BF16
+ * hi/lo split of the transpose that the tensor-core Gram reads).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers documented "device" must be device memory of the handle's
+ *    device; "host" pointers are ordinary host memory.  The caller owns every
+ *    input and output buffer.  The library owns only scratch memory, which it
+ *    allocates lazily inside the handle and frees in gmgm_destroy.
+ *  - Matrices are row-major with an explicit leading dimension (elements).
+ *  - Work is enqueued on the handle's stream and the call returns without
+ *    synchronising, unless a host-side stats pointer is passed (documented
+ *    per call), in which case the call synchronises the stream to fill it.
+ *  - Return value: GMGM_OK or a negative gmgm_status.  Argument errors are
+ *    detected on the host before anything is enqueued (GMGM_E_ARG; nothing
+ *    is modified).  Errors found on the device (non-finite values, solver not
+ *    converged, spin-wait timeout) set bits of a device status word that
+ *    gmgm_device_status() returns after synchronising.  gmgm_last_error()
+ *    gives a message for the last failure.  Invalid input is never silently
+ *    repaired, and there is no CPU fallback.
+ */
+#ifndef GMGM_H_
+#define GMGM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmgm_handle gmgm_handle;
+
+typedef enum {
+  GMGM_OK = 0,
+  GMGM_E_ARG = -1,            /* invalid argument (host-detected) */
+  GMGM_E_CUDA = -2,           /* a CUDA runtime call failed */
+  GMGM_E_NOMEM = -3,          /* scratch allocation failed */
+  GMGM_E_NONFINITE = -4,      /* NaN/Inf met on the device */
+  GMGM_E_NOT_CONVERGED = -5,  /* eigenvalue solve hit its iteration cap */
+  GMGM_E_INFEASIBLE = -6,     /* no feasible step (all s > 0 lost) */
+  GMGM_E_CAND_OVERFLOW = -7,  /* top-k screen could not certify a row */
+  GMGM_E_TIMEOUT = -8         /* a bounded device spin-wait gave up */
+} gmgm_status;
+
+/* Device status word bits (gmgm_device_status returns their OR, or 0). */
+#define GMGM_DEV_NONFINITE 0x1
+#define GMGM_DEV_NOT_CONVERGED 0x2
+#define GMGM_DEV_INFEASIBLE 0x4
+#define GMGM_DEV_CAND_OVERFLOW 0x8
+#define GMGM_DEV_TIMEOUT 0x10
+
+typedef enum {
+  GMGM_FP32 = 0,   /* FP32 SIMT arithmetic (the plain comparator form) */
+  GMGM_BF16 = 1,   /* BF16 tensor-core products, FP32 accumulation */
+  GMGM_BF16X3 = 2, /* 3xBF16 split products (hi*hi + hi*lo + lo*hi), FP32 acc. */
+  GMGM_FP64 = 3
+} gmgm_prec;
+
+/* ---- handle ------------------------------------------------------------ */
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *h receives the
+ * handle.  Returns GMGM_E_CUDA if the device cannot be selected. */
+int gmgm_create(gmgm_handle** h, int device, void* cuda_stream);
+
+/* Synchronise the handle's stream, free its scratch memory and the handle. */
+int gmgm_destroy(gmgm_handle* h);
+
+/* Re-bind the handle to another stream of the same device. */
+int gmgm_set_stream(gmgm_handle* h, void* cuda_stream);
+
+/* Message for the last non-OK return on this handle ("" if none).  The
+ * string is owned by the handle and valid until the next call on it. */
+const char* gmgm_last_error(const gmgm_handle* h);
+
+/* Synchronise the handle's stream, then return and clear the device status
+ * word (an OR of GMGM_DEV_* bits; 0 = no device-side error).  A negative
+ * value is a gmgm_status for a failed synchronisation. */
+int gmgm_device_status(gmgm_handle* h);
+
+/* Library version string, e.g. "gmgm 0.1 sm_103a". */
+const char* gmgm_version(void);
+
+/* ---- preprocessing ------------------------------------------------------ */
+
+/* X = log1p(counts) - column means, for an n x p count matrix (cells x genes).
+ *   counts  device, n x p FP32, leading dimension ldc >= p.
+ *   x_out   device, n x p FP32, leading dimension ldx >= p; may alias counts
+ *           (then ldx must equal ldc).
+ *   xt_hi, xt_lo  device, optional (both NULL or both set): the BF16 split of
+ *           X^T, p x ld_t row-major (gene-major), hi = bf16(x),
+ *           lo = bf16(x - hi); columns n..ld_t-1 are written as zero.
+ *           ld_t >= n and a multiple of 64 (the tensor-core K tile).
+ *   colmean_out  device, optional, p FP64 column means of log1p(counts).
+ * The paper's own transform is the Nonparanormal Skeptic (Section "The
+ * model"); the log1p + centring used here is the transform of the scRNA-like
+ * workloads.  Errors: GMGM_E_ARG for n < 2, p < 1, bad strides/alignment. */
+int gmgm_preprocess(gmgm_handle* h, int64_t n, int64_t p,
+                    const float* counts, int64_t ldc,
+                    float* x_out, int64_t ldx,
+                    uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t,
+                    double* colmean_out);
+
+/* ---- step 1: Gram ------------------------------------------------------- */
+
+/* A batch of equally shaped matrices X_b (rows x cols), b < batch. */
+typedef struct {
+  int64_t batch;          /* >= 1 */
+  int64_t rows, cols;     /* shape of each X_b */
+  int64_t ld;             /* row stride of X_b in elements (>= cols) */
+  int64_t batch_stride;   /* elements from X_b to X_{b+1} */
+  const float* x;         /* device FP32 data (used by GMGM_FP32) */
+  const uint16_t* xt_hi;  /* device BF16 hi split of X^T: cols x ld_t
+                             (used by GMGM_BF16 / GMGM_BF16X3; batch == 1) */
+  const uint16_t* xt_lo;  /* device BF16 lo split (GMGM_BF16X3) */
+  int64_t ld_t;           /* leading dimension of xt_* (>= rows, % 64 == 0) */
+} gmgm_matrix;
+
+#define GMGM_SIDE_COLS 0  /* S = sum_b X_b^T X_b  (cols x cols) */
+#define GMGM_SIDE_ROWS 1  /* S = sum_b X_b X_b^T  (rows x rows) */
+
+/* Axis Gram S_l = mat_l[D] mat_l[D]^T (Notation section; Section
+ * "Algorithm" for the sum over modalities = Gram of the concatenation).
+ * For a matrix (cells x genes) S_genes = X^T X is side GMGM_SIDE_COLS; for a
+ * 3-axis tensor T (d0 x d1 x d2, row-major) the three Grams are
+ *   axis 0: one matrix d0 x (d1 d2), side ROWS;
+ *   axis 1: batch d0 of d1 x d2 slices, side ROWS;
+ *   axis 2: one matrix (d0 d1) x d2, side COLS.
+ * S is written (accumulate = 0) or added to (accumulate = 1), FP64, device,
+ * leading dimension lds; both triangles are written.  Partial sums are
+ * formed in `prec` arithmetic and combined in FP64.  GMGM_SIDE_ROWS supports
+ * GMGM_FP32 only.  Errors: GMGM_E_ARG (shape/stride/precision). */
+int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec,
+              double* S, int64_t lds, int accumulate);
+
+/* ---- step 2: spectra ---------------------------------------------------- */
+
+/* Symmetric FP64 eigendecomposition of S (d x d, device, leading dimension
+ * lds; only the lower triangle is read) on the GPU: Householder
+ * tridiagonalisation, bisection for the eigenvalues, inverse iteration with
+ * re-orthogonalisation of close clusters for the vectors, and the
+ * back-transformation.  Theorem 1: the top-r eigenvectors of S_l are those of
+ * the MLE Psi_l.
+ *   evals  device, r FP64, the r largest eigenvalues, descending.
+ *   evecs  device, d x r FP64 row-major (column c is the eigenvector of
+ *          evals[c]), leading dimension ldv >= r; may be NULL (values only).
+ * 1 <= r <= d <= 8192.  Eigenvector signs are arbitrary.  The call uses a
+ * cooperative launch.  Errors: GMGM_E_ARG, GMGM_E_CUDA; device TIMEOUT bit
+ * if a grid barrier gave up. */
+int gmgm_spectra(gmgm_handle* h, int64_t d, const double* S, int64_t lds,
+                 int32_t r, double* evals, double* evecs, int64_t ldv);
+
+/* Dual lift (Section "Algorithm": eigenvectors of S_l are singular vectors
+ * of mat_l[D]; Algorithm 1 takes the top-r left singular vectors): for the
+ * matrix X (rows x cols, FP32 m->x) and the top-r eigenpairs (W, E) of
+ * X^T X, U = X W diag(E)^-1/2 are the top-r eigenvectors of X X^T.
+ *   W      device, cols x r FP64 row-major, leading dimension ldw.
+ *   E      device, r FP64, all > 0.
+ *   U      device, rows x r FP32 row-major, leading dimension ldu >= r.
+ * Errors: GMGM_E_ARG (batch != 1, shapes). */
+int gmgm_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r,
+              const double* W, int64_t ldw, const double* E,
+              float* U, int64_t ldu);
+
+/* ---- step 3: eigenvalue solve ------------------------------------------- */
+
+#define GMGM_MAX_AXES 4
+#define GMGM_MAX_MODALITIES 4
+
+/* The eigenvalue problem: per-axis spectra E_l (descending, > 0) and the
+ * modalities, each a list of axis indices in tensor order.  Objective
+ * (twice the NLL, constants dropped):
+ *   f(Lam) = sum_l E_l . Lam_l - sum_gamma sum_{grid of gamma} log s,
+ *   s(i_1, i_2, ...) = sum_{l in gamma} lam_{l, i_l},
+ * over the box lam_l,i >= eps_l. */
+typedef struct {
+  int32_t n_axes;                     /* 1..GMGM_MAX_AXES */
+  int32_t r[GMGM_MAX_AXES];           /* ranks r_l >= 1 */
+  const double* E[GMGM_MAX_AXES];     /* device, r_l FP64 each */
+  double eps[GMGM_MAX_AXES];          /* box; <= 0 selects the default:
+                                         1e-10 * max over modalities of
+                                         sum_l max_i 1/E_l,i (same for all l) */
+  int32_t n_modalities;               /* 1..GMGM_MAX_MODALITIES */
+  int32_t mod_n_axes[GMGM_MAX_MODALITIES];
+  int32_t mod_axes[GMGM_MAX_MODALITIES][GMGM_MAX_AXES];
+} gmgm_problem;
+
+typedef struct {
+  double tol;           /* relative projected-KKT target, max_i |P(g)_i|/E_i
+                           (<= 0: 1e-9) */
+  int32_t max_newton;   /* Newton iteration cap (<= 0: 200) */
+  int32_t max_cg;       /* CG iterations per Newton step (<= 0: 200) */
+  int32_t fp32_phase;   /* 1: iterate in FP32 (Kahan/FP64 partials) until
+                           rel. KKT <= 1e-5, then FP64; 0: FP64 throughout */
+  int32_t gauge;        /* 1: apply the gauge convention (flat shift, single
+                           modality with equal traces): every axis but the
+                           first gets min = eps.  0: leave as solved. */
+} gmgm_solve_opts;
+
+typedef struct {
+  int32_t status;       /* GMGM_OK, GMGM_E_NOT_CONVERGED, ... */
+  int32_t newton_iters;
+  int32_t cg_iters;     /* total Hessian-vector products */
+  int32_t grid_passes;  /* total passes over the Kronecker-sum grids */
+  int32_t n_active;     /* coordinates at their bound */
+  int32_t fp64_iters;   /* Newton iterations run in FP64 */
+  double rel_kkt;       /* final FP64 relative projected-KKT residual */
+  double objective;     /* final f(Lam), FP64 */
+} gmgm_solve_stats;
+
+/* Solve for the eigenvalues Lam_l of the MLE (Proposition on the gradient:
+ * g_l,i = E_l,i - sum_{gamma containing l} sum_{other indices} 1/s; the
+ * existence lemma's box Lam_l >= eps_l).  One persistent single-CTA kernel
+ * runs a projected Newton method (Bertsekas' active set; conjugate gradients
+ * on the free set with Hessian-vector products computed as grid reductions;
+ * Armijo search along the projection arc) and the final KKT check in FP64.
+ *   init        host array of n_axes device pointers (r_l FP64 each) for the
+ *               starting point, or NULL for Algorithm 1's Lam^0 = 1/E.
+ *   lambda_out  host array of n_axes device pointers (r_l FP64 each).
+ *   stats       host, optional; if non-NULL the call synchronises and fills
+ *               it (and returns its status).
+ * Sizes: sum_l r_l <= 16384; every modality grid <= 2^31 points.
+ * Errors: GMGM_E_ARG; device bits NOT_CONVERGED / INFEASIBLE / NONFINITE. */
+int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p,
+                  const double* const* init, const gmgm_solve_opts* opts,
+                  double* const* lambda_out, gmgm_solve_stats* stats);
+
+/* ---- step 4: recomposition + per-row top-k ------------------------------ */
+
+typedef struct {
+  int64_t rows_uncertified;  /* rows whose screen margin did not certify the
+                                top-k and that were recomputed exactly */
+  int64_t candidates;        /* candidate slots per row used by the screen */
+  double screen_ms;          /* device time of the screen kernel */
+  double rescore_ms;         /* device time of rescoring (+ repair) */
+} gmgm_topk_stats;
+
+/* Per-row top-k of Psi = V diag(psi) V^T without forming Psi (Algorithm 1:
+ * thresh_{n_l}[V_l Lam_l V_l^T], "threshold simultaneously with
+ * recomposition").  Readings: an edge's strength is |Psi_ij|; the diagonal
+ * is excluded; each row keeps its own k edges; equal magnitudes are ordered
+ * by the lower column index.
+ *   V       device, d x r row-major, FP32 (v_fp64 = 0) or FP64 (v_fp64 = 1),
+ *           leading dimension ldv >= r.
+ *   psi     device, r FP64 eigenvalues.
+ *   k       1 <= k <= 32 and k < d.
+ *   prec    screen arithmetic: GMGM_FP32 (SIMT), GMGM_BF16 or GMGM_BF16X3
+ *           (tcgen05 tensor cores).
+ *   idx_out device, d x k int32: column indices, by |Psi_ij| descending.
+ *   val_out device, d x k FP32: the signed Psi_ij, computed in FP64 from V
+ *           (as given) and psi, then rounded.
+ *   stats   host, optional; if non-NULL the call synchronises and fills it.
+ * Exactness: every row's screen is certified with a rigorous error bound of
+ * the screen arithmetic (the k-th exact value must beat the best excluded
+ * screened value plus the bound); rows that fail are recomputed in FP64, so
+ * idx_out is the exact FP64 top-k of the given V and psi.
+ * Errors: GMGM_E_ARG. */
+int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r,
+                      const void* V, int v_fp64, int64_t ldv,
+                      const double* psi, int32_t k, gmgm_prec prec,
+                      int32_t* idx_out, float* val_out,
+                      gmgm_topk_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMGM_H_ */

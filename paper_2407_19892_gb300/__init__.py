@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) implementation of the data-parallel core of the improved
+multi-axis Gaussian graphical model fit (GmGM, arXiv 2407.19892).
+
+The compute path is the CUDA library ``libgmgm`` (C ABI in include/gmgm.h);
+this package holds its build script and a thin ctypes binding.
+"""
+
+from ._lib import (BF16, BF16X3, FP32, FP64, SIDE_COLS, SIDE_ROWS,  # noqa: F401
+                   GmgmError, load)
+from .api import (Handle, TwoAxisResult, eigsolve, fit_two_axis, gram,  # noqa: F401
+                  handle, lift, preprocess, spectra, topk_network)
+
+__version__ = "0.1.0"

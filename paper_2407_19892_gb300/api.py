@@ -1,0 +1,269 @@
+"""Python surface over the C ABI: torch device tensors in, torch tensors out.
+
+Every step of the fit runs in the library's CUDA kernels; this module only
+allocates outputs with PyTorch (device memory), passes pointers and the
+current stream, and checks return codes.
+"""
+
+import ctypes
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Handle:
+    """A library handle bound to a CUDA device and (by default) torch's
+    current stream on it."""
+
+    def __init__(self, device=None, stream=None):
+        self.lib = L.load()
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if dev.type != "cuda":
+            raise ValueError("gmgm needs a CUDA device")
+        self.device = dev
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.gmgm_create(ctypes.byref(h), dev.index or 0, ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise L.GmgmError(rc, "gmgm_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gmgm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def check(self, rc):
+        if rc != 0:
+            msg = self.lib.gmgm_last_error(self.h).decode()
+            raise L.GmgmError(rc, msg)
+
+    def device_status(self):
+        """Synchronise and return (and clear) the device status bits."""
+        rc = self.lib.gmgm_device_status(self.h)
+        if rc < 0:
+            self.check(rc)
+        return rc
+
+
+_default = {}
+
+
+def handle(device=None) -> Handle:
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    key = (dev.index or 0, torch.cuda.current_stream(dev).cuda_stream)
+    h = _default.get(key)
+    if h is None:
+        h = Handle(dev)
+        _default[key] = h
+    return h
+
+
+def _need_cuda(t, dtype, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+
+
+# ---- preprocessing ----------------------------------------------------------
+
+def preprocess(counts: torch.Tensor, split: bool = True, inplace: bool = False, h: Handle = None):
+    """log1p + column centring of an n x p FP32 count matrix on the GPU.
+    Returns (X, xt_hi, xt_lo, ld_t); xt_* are p x ld_t BF16 planes of X^T
+    (None when split=False)."""
+    h = h or handle(counts.device)
+    _need_cuda(counts, torch.float32, "counts")
+    if counts.dim() != 2 or counts.stride(1) != 1:
+        raise ValueError("counts must be a row-major 2-D tensor")
+    n, p = counts.shape
+    x = counts if inplace else torch.empty_like(counts)
+    hi = lo = None
+    ld_t = 0
+    if split:
+        ld_t = ((n + 63) // 64) * 64
+        hi = torch.empty(p, ld_t, dtype=torch.bfloat16, device=counts.device)
+        lo = torch.empty(p, ld_t, dtype=torch.bfloat16, device=counts.device)
+    h.check(h.lib.gmgm_preprocess(h.h, n, p, _ptr(counts), counts.stride(0), _ptr(x), x.stride(0),
+                                  _ptr(hi), _ptr(lo), ld_t, None))
+    return x, hi, lo, ld_t
+
+
+# ---- Gram ------------------------------------------------------------------
+
+def _matrix(x=None, xt_hi=None, xt_lo=None, ld_t=0, rows=None, cols=None, batch=1, batch_stride=0):
+    m = L.Matrix()
+    if x is not None:
+        if x.dim() == 2:
+            rows, cols = x.shape
+            m.ld = x.stride(0)
+        elif x.dim() == 3:
+            batch, rows, cols = x.shape
+            m.ld = x.stride(1)
+            batch_stride = x.stride(0)
+        else:
+            raise ValueError("x must be 2-D or 3-D")
+        if x.stride(-1) != 1:
+            raise ValueError("x must have unit stride in its last dimension")
+        m.x = x.data_ptr()
+    m.batch, m.rows, m.cols, m.batch_stride = batch, rows, cols, batch_stride
+    m.xt_hi = xt_hi.data_ptr() if xt_hi is not None else None
+    m.xt_lo = xt_lo.data_ptr() if xt_lo is not None else None
+    m.ld_t = ld_t
+    return m
+
+
+def gram(x: torch.Tensor = None, side: int = L.SIDE_COLS, prec: int = L.FP32, xt_hi=None, xt_lo=None,
+         ld_t: int = 0, rows: int = None, cols: int = None, out: torch.Tensor = None, accumulate=False,
+         h: Handle = None):
+    """S = sum_b X_b^T X_b (side COLS) or sum_b X_b X_b^T (side ROWS), FP64."""
+    dev = x.device if x is not None else xt_hi.device
+    h = h or handle(dev)
+    if x is not None:
+        _need_cuda(x, torch.float32, "x")
+    m = _matrix(x, xt_hi, xt_lo, ld_t, rows, cols)
+    d = m.cols if side == L.SIDE_COLS else m.rows
+    if out is None:
+        out = torch.empty(d, d, dtype=torch.float64, device=dev)
+    h.check(h.lib.gmgm_gram(h.h, ctypes.byref(m), side, prec, _ptr(out), out.stride(0), int(accumulate)))
+    return out
+
+
+# ---- spectra ---------------------------------------------------------------
+
+def spectra(S: torch.Tensor, r: int, vectors: bool = True, h: Handle = None):
+    """Top-r eigenpairs (descending) of a symmetric FP64 matrix on the GPU."""
+    h = h or handle(S.device)
+    _need_cuda(S, torch.float64, "S")
+    d = S.shape[0]
+    ev = torch.empty(r, dtype=torch.float64, device=S.device)
+    W = torch.empty(d, r, dtype=torch.float64, device=S.device) if vectors else None
+    h.check(h.lib.gmgm_spectra(h.h, d, _ptr(S), S.stride(0), r, _ptr(ev), _ptr(W), r))
+    return ev, W
+
+
+def lift(x: torch.Tensor, W: torch.Tensor, E: torch.Tensor, r: int, h: Handle = None):
+    """U = X W_r diag(E_r)^-1/2 (rows x r, FP32)."""
+    h = h or handle(x.device)
+    _need_cuda(x, torch.float32, "x")
+    m = _matrix(x)
+    U = torch.empty(x.shape[0], r, dtype=torch.float32, device=x.device)
+    h.check(h.lib.gmgm_lift(h.h, ctypes.byref(m), r, _ptr(W), W.stride(0), _ptr(E), _ptr(U), r))
+    return U
+
+
+# ---- eigenvalue solve --------------------------------------------------------
+
+def eigsolve(E, modalities=None, eps=None, init=None, tol=1e-9, max_newton=200, max_cg=200,
+             fp32_phase=True, gauge=True, h: Handle = None):
+    """Eigenvalues Lam_l of the MLE.  E: list of FP64 CUDA tensors (descending
+    spectra); modalities: list of tuples of axis indices (default: one
+    modality over all axes).  Returns (list of FP64 tensors, stats dict)."""
+    E = [e.contiguous() for e in E]
+    dev = E[0].device
+    h = h or handle(dev)
+    for e in E:
+        _need_cuda(e, torch.float64, "E")
+    if modalities is None:
+        modalities = [tuple(range(len(E)))]
+    p = L.Problem()
+    p.n_axes = len(E)
+    for a, e in enumerate(E):
+        p.r[a] = e.numel()
+        p.E[a] = e.data_ptr()
+        p.eps[a] = eps[a] if eps is not None else 0.0
+    p.n_modalities = len(modalities)
+    for g, m in enumerate(modalities):
+        p.mod_n_axes[g] = len(m)
+        for q, a in enumerate(m):
+            p.mod_axes[g][q] = a
+    outs = [torch.empty_like(e) for e in E]
+    out_arr = (ctypes.c_void_p * len(E))(*[o.data_ptr() for o in outs])
+    init_arr = None
+    if init is not None:
+        init = [t.contiguous() for t in init]
+        init_arr = (ctypes.c_void_p * len(E))(*[t.data_ptr() for t in init])
+    o = L.SolveOpts(tol, max_newton, max_cg, int(fp32_phase), int(gauge))
+    st = L.SolveStats()
+    rc = h.lib.gmgm_eigsolve(h.h, ctypes.byref(p), init_arr, ctypes.byref(o), out_arr, ctypes.byref(st))
+    if rc not in (0, -5):
+        h.check(rc)
+    return outs, st.as_dict()
+
+
+# ---- top-k network -------------------------------------------------------------
+
+def topk_network(V: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32, h: Handle = None):
+    """Per-row top-k of |V diag(psi) V^T| (diagonal excluded).  Returns
+    (idx int32 [d, k], val float32 [d, k], stats dict)."""
+    h = h or handle(V.device)
+    if V.dtype not in (torch.float32, torch.float64) or not V.is_cuda or V.stride(1) != 1:
+        raise ValueError("V must be a row-major CUDA FP32/FP64 matrix")
+    _need_cuda(psi, torch.float64, "psi")
+    d, r = V.shape
+    idx = torch.empty(d, k, dtype=torch.int32, device=V.device)
+    val = torch.empty(d, k, dtype=torch.float32, device=V.device)
+    st = L.TopkStats()
+    h.check(h.lib.gmgm_topk_network(h.h, d, r, _ptr(V), int(V.dtype == torch.float64), V.stride(0),
+                                    _ptr(psi.contiguous()), k, prec, _ptr(idx), _ptr(val),
+                                    ctypes.byref(st)))
+    return idx, val, st.as_dict()
+
+
+# ---- the whole two-axis fit -----------------------------------------------------
+
+@dataclass
+class TwoAxisResult:
+    e_rows: torch.Tensor
+    v_rows: torch.Tensor
+    e_cols: torch.Tensor
+    v_cols: torch.Tensor
+    lam_rows: torch.Tensor
+    lam_cols: torch.Tensor
+    idx_rows: torch.Tensor
+    val_rows: torch.Tensor
+    idx_cols: torch.Tensor
+    val_cols: torch.Tensor
+    solve: dict = field(default_factory=dict)
+    topk_rows_stats: dict = field(default_factory=dict)
+    topk_cols_stats: dict = field(default_factory=dict)
+
+
+def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols: int,
+                 gram_prec: int = L.FP32, topk_prec: int = L.FP32, xt_hi=None, xt_lo=None, ld_t=0,
+                 tol: float = 1e-9, fp32_phase=True, init=None, h: Handle = None) -> TwoAxisResult:
+    """Algorithm 1 on a centred matrix X (rows x cols, FP32, on the GPU):
+    S_cols = X^T X, its eigenpairs (FP64), the row-axis vectors by the dual
+    lift, the eigenvalue solve, and both per-row top-k networks."""
+    h = h or handle(x.device)
+    S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, h=h)
+    rmax = max(r_rows, r_cols)
+    ev, W = spectra(S, rmax, True, h=h)
+    e_cols, v_cols = ev[:r_cols].contiguous(), W[:, :r_cols].contiguous()
+    e_rows = ev[:r_rows].contiguous()
+    v_rows = lift(x, W[:, :r_rows].contiguous(), e_rows, r_rows, h=h)
+    (lam_rows, lam_cols), st = eigsolve([e_rows, e_cols], [(0, 1)], tol=tol, fp32_phase=fp32_phase,
+                                        init=init, h=h)
+    ir, vr, sr = topk_network(v_rows, lam_rows, k_rows, topk_prec, h=h)
+    ic, vc, sc = topk_network(v_cols, lam_cols, k_cols, L.FP32, h=h)
+    return TwoAxisResult(e_rows, v_rows, e_cols, v_cols, lam_rows, lam_cols, ir, vr, ic, vc, st, sr, sc)

@@ -1,0 +1,267 @@
+// C-ABI entry points: argument checks, scratch management and dispatch.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+namespace gmgm {
+
+int fail(gmgm_handle* h, int code, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return code;
+}
+
+int ensure_scratch(gmgm_handle* h, size_t bytes) {
+  if (bytes <= h->scratch_bytes) return GMGM_OK;
+  if (h->scratch) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->scratch);
+    h->scratch = nullptr;
+    h->scratch_bytes = 0;
+  }
+  size_t want = bytes + (bytes >> 3);
+  cudaError_t e = cudaMalloc(&h->scratch, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, GMGM_E_NOMEM, std::string("scratch cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->scratch_bytes = want;
+  return GMGM_OK;
+}
+
+}  // namespace gmgm
+
+using gmgm::fail;
+
+extern "C" {
+
+const char* gmgm_version(void) { return "gmgm 0.1 sm_103a"; }
+
+int gmgm_create(gmgm_handle** out, int device, void* stream) {
+  if (!out) return GMGM_E_ARG;
+  *out = nullptr;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return GMGM_E_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return GMGM_E_CUDA;
+  }
+  gmgm_handle* h = new gmgm_handle();
+  h->device = device;
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&h->d_status, 64) != cudaSuccess ||
+      cudaMalloc(&h->d_barrier, 64) != cudaSuccess ||
+      cudaMemset(h->d_status, 0, 64) != cudaSuccess ||
+      cudaMemset(h->d_barrier, 0, 64) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->d_status) cudaFree(h->d_status);
+    if (h->d_barrier) cudaFree(h->d_barrier);
+    delete h;
+    cudaSetDevice(cur);
+    return GMGM_E_CUDA;
+  }
+  cudaSetDevice(cur);
+  *out = h;
+  return GMGM_OK;
+}
+
+int gmgm_destroy(gmgm_handle* h) {
+  if (!h) return GMGM_E_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->scratch) cudaFree(h->scratch);
+  cudaFree(h->d_status);
+  cudaFree(h->d_barrier);
+  cudaSetDevice(cur);
+  delete h;
+  return GMGM_OK;
+}
+
+int gmgm_set_stream(gmgm_handle* h, void* stream) {
+  if (!h) return GMGM_E_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return GMGM_OK;
+}
+
+const char* gmgm_last_error(const gmgm_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
+
+int gmgm_device_status(gmgm_handle* h) {
+  if (!h) return GMGM_E_ARG;
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  GMGM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  int st = 0;
+  GMGM_CUDA_TRY(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  GMGM_CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(int)));
+  return st;
+}
+
+int gmgm_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc,
+                    float* x_out, int64_t ldx, uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t,
+                    double* colmean_out) {
+  if (!h) return GMGM_E_ARG;
+  if (n < 2 || p < 1 || !counts || !x_out || ldc < p || ldx < p)
+    return fail(h, GMGM_E_ARG, "gmgm_preprocess: need n >= 2, p >= 1, ldc, ldx >= p, non-null buffers");
+  if ((const void*)counts == (const void*)x_out && ldc != ldx)
+    return fail(h, GMGM_E_ARG, "gmgm_preprocess: in-place needs ldx == ldc");
+  if ((xt_hi == nullptr) != (xt_lo == nullptr))
+    return fail(h, GMGM_E_ARG, "gmgm_preprocess: xt_hi and xt_lo must both be set or both NULL");
+  if (xt_hi && (ld_t < n || ld_t % 64 != 0 || ((uintptr_t)xt_hi % 16) || ((uintptr_t)xt_lo % 16)))
+    return fail(h, GMGM_E_ARG, "gmgm_preprocess: ld_t must be >= n, a multiple of 64, 16-byte aligned xt");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, size_t(p) * sizeof(double) + 256);
+  if (rc) return rc;
+  GMGM_CUDA_TRY(h, gmgm::launch_preprocess(h, n, p, counts, ldc, x_out, ldx, xt_hi, xt_lo, ld_t,
+                                           static_cast<double*>(h->scratch), colmean_out));
+  return GMGM_OK;
+}
+
+int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec, double* S,
+              int64_t lds, int accumulate) {
+  if (!h) return GMGM_E_ARG;
+  if (!m || !S || m->batch < 1 || m->rows < 1 || m->cols < 1)
+    return fail(h, GMGM_E_ARG, "gmgm_gram: null argument or empty shape");
+  if (side != GMGM_SIDE_COLS && side != GMGM_SIDE_ROWS)
+    return fail(h, GMGM_E_ARG, "gmgm_gram: side must be GMGM_SIDE_COLS or GMGM_SIDE_ROWS");
+  const int64_t dS = side == GMGM_SIDE_COLS ? m->cols : m->rows;
+  if (lds < dS) return fail(h, GMGM_E_ARG, "gmgm_gram: lds < size of S");
+  if (dS > 65536) return fail(h, GMGM_E_ARG, "gmgm_gram: S larger than 65536 x 65536");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  if (prec == GMGM_FP32) {
+    if (!m->x || m->ld < m->cols || (m->batch > 1 && m->batch_stride < m->rows * m->ld))
+      return fail(h, GMGM_E_ARG, "gmgm_gram: FP32 needs x, ld >= cols, batch_stride >= rows*ld");
+    int splits = gmgm::gram_fp32_splits(h, m, side);
+    int rc = gmgm::ensure_scratch(h, gmgm::gram_fp32_scratch_bytes(dS, splits));
+    if (rc) return rc;
+    GMGM_CUDA_TRY(h, gmgm::launch_gram_fp32(h, m, side, S, lds, accumulate,
+                                            static_cast<float*>(h->scratch), splits));
+    return GMGM_OK;
+  }
+  if (prec == GMGM_BF16 || prec == GMGM_BF16X3) {
+    if (side != GMGM_SIDE_COLS || m->batch != 1)
+      return fail(h, GMGM_E_ARG, "gmgm_gram: tensor-core Gram supports side COLS, batch 1");
+    if (!m->xt_hi || (prec == GMGM_BF16X3 && !m->xt_lo) || m->ld_t < m->rows || m->ld_t % 64)
+      return fail(h, GMGM_E_ARG, "gmgm_gram: BF16 needs xt_hi (+ xt_lo for BF16X3), ld_t >= rows, % 64");
+    if (((uintptr_t)m->xt_hi % 16) || (m->xt_lo && ((uintptr_t)m->xt_lo % 16)))
+      return fail(h, GMGM_E_ARG, "gmgm_gram: xt buffers must be 16-byte aligned");
+    int splits = gmgm::gram_tc_splits(h, m);
+    size_t tiles = size_t((m->cols + 127) / 128);
+    size_t bytes = size_t(splits) * tiles * tiles * 128 * 128 * sizeof(float);
+    int rc = gmgm::ensure_scratch(h, bytes + 256);
+    if (rc) return rc;
+    GMGM_CUDA_TRY(h, gmgm::launch_gram_tc(h, m, prec, S, lds, accumulate,
+                                          static_cast<float*>(h->scratch), splits));
+    return GMGM_OK;
+  }
+  return fail(h, GMGM_E_ARG, "gmgm_gram: unsupported precision");
+}
+
+int gmgm_spectra(gmgm_handle* h, int64_t d, const double* S, int64_t lds, int32_t r,
+                 double* evals, double* evecs, int64_t ldv) {
+  if (!h) return GMGM_E_ARG;
+  if (d < 1 || d > 8192 || r < 1 || r > d || !S || !evals || lds < d || (evecs && ldv < r))
+    return fail(h, GMGM_E_ARG, "gmgm_spectra: need 1 <= r <= d <= 8192, lds >= d, ldv >= r");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, gmgm::eig_scratch_bytes(d, r));
+  if (rc) return rc;
+  GMGM_CUDA_TRY(h, gmgm::launch_eig(h, d, S, lds, r, evals, evecs, ldv, h->scratch));
+  return GMGM_OK;
+}
+
+int gmgm_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const double* W, int64_t ldw,
+              const double* E, float* U, int64_t ldu) {
+  if (!h) return GMGM_E_ARG;
+  if (!m || !m->x || m->batch != 1 || m->rows < 1 || m->cols < 1 || m->ld < m->cols)
+    return fail(h, GMGM_E_ARG, "gmgm_lift: need one FP32 matrix");
+  if (r < 1 || r > 256 || r > m->cols || !W || !E || !U || ldw < r || ldu < r)
+    return fail(h, GMGM_E_ARG, "gmgm_lift: need 1 <= r <= min(256, cols), ldw, ldu >= r");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, size_t(m->cols) * r * sizeof(float) + 256);
+  if (rc) return rc;
+  GMGM_CUDA_TRY(h, gmgm::launch_lift(h, m, r, W, ldw, E, U, ldu, static_cast<float*>(h->scratch)));
+  return GMGM_OK;
+}
+
+int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p, const double* const* init,
+                  const gmgm_solve_opts* o, double* const* lambda_out, gmgm_solve_stats* stats) {
+  if (!h) return GMGM_E_ARG;
+  if (!p || !lambda_out) return fail(h, GMGM_E_ARG, "gmgm_eigsolve: null problem or output");
+  if (p->n_axes < 1 || p->n_axes > GMGM_MAX_AXES || p->n_modalities < 1 ||
+      p->n_modalities > GMGM_MAX_MODALITIES)
+    return fail(h, GMGM_E_ARG, "gmgm_eigsolve: bad axis or modality count");
+  int64_t total = 0;
+  for (int a = 0; a < p->n_axes; ++a) {
+    if (p->r[a] < 1 || !p->E[a] || !lambda_out[a] || (init && !init[a]))
+      return fail(h, GMGM_E_ARG, "gmgm_eigsolve: bad rank or null pointer for an axis");
+    total += p->r[a];
+  }
+  if (total > 16384) return fail(h, GMGM_E_ARG, "gmgm_eigsolve: sum of ranks > 16384");
+  int used[GMGM_MAX_AXES] = {0, 0, 0, 0};
+  for (int g = 0; g < p->n_modalities; ++g) {
+    int k = p->mod_n_axes[g];
+    if (k < 1 || k > GMGM_MAX_AXES) return fail(h, GMGM_E_ARG, "gmgm_eigsolve: bad modality size");
+    int64_t pts = 1;
+    int seen = 0;
+    for (int q = 0; q < k; ++q) {
+      int a = p->mod_axes[g][q];
+      if (a < 0 || a >= p->n_axes || (seen & (1 << a)))
+        return fail(h, GMGM_E_ARG, "gmgm_eigsolve: bad or repeated axis in a modality");
+      seen |= 1 << a;
+      used[a] = 1;
+      pts *= p->r[a];
+    }
+    if (pts > (int64_t(1) << 31)) return fail(h, GMGM_E_ARG, "gmgm_eigsolve: grid too large");
+  }
+  for (int a = 0; a < p->n_axes; ++a)
+    if (!used[a]) return fail(h, GMGM_E_ARG, "gmgm_eigsolve: an axis is in no modality");
+  gmgm_solve_opts opt = {1e-9, 200, 200, 1, 1};
+  if (o) {
+    opt = *o;
+    if (opt.tol <= 0) opt.tol = 1e-9;
+    if (opt.max_newton <= 0) opt.max_newton = 200;
+    if (opt.max_cg <= 0) opt.max_cg = 200;
+  }
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  size_t need = gmgm::solve_scratch_bytes(p) + sizeof(gmgm_solve_stats) + 512;
+  int rc = gmgm::ensure_scratch(h, need);
+  if (rc) return rc;
+  gmgm_solve_stats* d_stats = reinterpret_cast<gmgm_solve_stats*>(
+      static_cast<char*>(h->scratch) + gmgm::Carve::round(gmgm::solve_scratch_bytes(p)));
+  GMGM_CUDA_TRY(h, gmgm::launch_solve(h, p, init, &opt, lambda_out, h->scratch, d_stats));
+  if (stats) {
+    GMGM_CUDA_TRY(h, cudaMemcpyAsync(stats, d_stats, sizeof(gmgm_solve_stats),
+                                     cudaMemcpyDeviceToHost, h->stream));
+    GMGM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (stats->status != GMGM_OK)
+      return fail(h, stats->status, "gmgm_eigsolve: device solve did not reach tolerance");
+  }
+  return GMGM_OK;
+}
+
+int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64,
+                      int64_t ldv, const double* psi, int32_t k, gmgm_prec prec,
+                      int32_t* idx_out, float* val_out, gmgm_topk_stats* stats) {
+  if (!h) return GMGM_E_ARG;
+  if (d < 2 || r < 1 || !V || !psi || !idx_out || !val_out || ldv < r)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network: need d >= 2, r >= 1, ldv >= r, non-null buffers");
+  if (k < 1 || k > 32 || k >= d) return fail(h, GMGM_E_ARG, "gmgm_topk_network: need 1 <= k <= 32, k < d");
+  if (d > (int64_t(1) << 31) - 1) return fail(h, GMGM_E_ARG, "gmgm_topk_network: d >= 2^31");
+  if (r > 4096) return fail(h, GMGM_E_ARG, "gmgm_topk_network: r > 4096");
+  if (prec != GMGM_FP32 && prec != GMGM_BF16 && prec != GMGM_BF16X3)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network: prec must be FP32, BF16 or BF16X3");
+  if (prec != GMGM_FP32 && r > 64)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network: tensor-core screen supports r <= 64");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, gmgm::topk_scratch_bytes(d, r, k, prec));
+  if (rc) return rc;
+  return gmgm::topk_run(h, d, r, V, v_fp64, ldv, psi, k, prec, idx_out, val_out, h->scratch, stats);
+}
+
+}  // extern "C"

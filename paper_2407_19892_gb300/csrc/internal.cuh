@@ -1,0 +1,91 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gmgm.h"
+
+struct gmgm_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  // device status word (OR of GMGM_DEV_* bits) + grid-barrier words
+  int* d_status = nullptr;
+  unsigned* d_barrier = nullptr;  // [0] = arrive count, [1] = generation
+  // lazily grown scratch arena
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  std::string last_error;
+};
+
+namespace gmgm {
+
+// Set the handle's message and return `code`.
+int fail(gmgm_handle* h, int code, const std::string& msg);
+
+// Ensure the scratch arena holds at least `bytes`; returns GMGM_OK or an
+// error (the arena is synchronised and re-allocated when it grows).
+int ensure_scratch(gmgm_handle* h, size_t bytes);
+
+// Bump allocator over the scratch arena (256-byte aligned slices).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+  static size_t round(size_t n) { return (n + 255) & ~size_t(255); }
+};
+
+// Check a CUDA call; on failure record the message and return GMGM_E_CUDA.
+#define GMGM_CUDA_TRY(h, call)                                               \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return ::gmgm::fail((h), GMGM_E_CUDA,                                  \
+                          std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---- kernel launchers (return cudaError_t of the launch) ----
+
+cudaError_t launch_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float* counts,
+                              int64_t ldc, float* x_out, int64_t ldx, uint16_t* xt_hi,
+                              uint16_t* xt_lo, int64_t ld_t, double* colsum_scratch,
+                              double* colmean_out);
+
+cudaError_t launch_gram_fp32(gmgm_handle* h, const gmgm_matrix* m, int side, double* S,
+                             int64_t lds, int accumulate, float* partials, int splits);
+int gram_fp32_splits(gmgm_handle* h, const gmgm_matrix* m, int side);
+size_t gram_fp32_scratch_bytes(int64_t dS, int splits);
+
+cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec, double* S,
+                           int64_t lds, int accumulate, float* partials, int splits);
+int gram_tc_splits(gmgm_handle* h, const gmgm_matrix* m);
+
+size_t eig_scratch_bytes(int64_t d, int32_t r);
+cudaError_t launch_eig(gmgm_handle* h, int64_t d, const double* S, int64_t lds, int32_t r,
+                       double* evals, double* evecs, int64_t ldv, void* scratch);
+
+cudaError_t launch_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const double* W,
+                        int64_t ldw, const double* E, float* U, int64_t ldu, float* wscr);
+
+struct SolveDesc;  // defined in k_solve.cu
+size_t solve_scratch_bytes(const gmgm_problem* p);
+cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* const* init,
+                         const gmgm_solve_opts* o, double* const* out, void* scratch,
+                         gmgm_solve_stats* d_stats);
+
+size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec);
+int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
+             const double* psi, int32_t k, gmgm_prec prec, int32_t* idx, float* val,
+             void* scratch, gmgm_topk_stats* st);
+
+}  // namespace gmgm

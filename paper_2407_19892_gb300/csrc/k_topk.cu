@@ -1,0 +1,382 @@
+// Recomposition + per-row top-k, Psi = V diag(psi) V^T never materialised
+// (Algorithm 1 last loop: threshold while recomposing).
+//
+// Every row is certified before it is trusted:
+//   screen   per-row candidate lists of the kC largest screened |Psi_ij|,
+//            j != i, over all columns: FP32 SIMT tiles here (the
+//            tensor-core screens live in k_topk_tc.cu);
+//   rescore  one warp per row recomputes every candidate in FP64 from V and
+//            psi, sorts (|value| desc, column asc) and certifies the row: the
+//            k-th exact value must exceed the best excluded screened value
+//            plus a rigorous bound on the screen's error;
+//   repair   rows that fail a tensor-core screen are screened again in FP32
+//            (rows gathered) and rescored; rows that still fail are scanned
+//            exactly in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+
+#include "device.cuh"
+#include "internal.cuh"
+#include "topk_common.cuh"
+
+namespace gmgm {
+namespace {
+
+constexpr int kBM = 128, kBN = 64, kBK = 32;
+
+// A = fl32(V * psi), B = fl32(V), both d x rpad, zero padded; colmax_k =
+// max_j |B_jk| as float bits (non-negative floats order like their bits).
+__global__ void prep_ab_kernel(const void* V, int v64, int64_t ldv, const double* __restrict__ psi, int64_t d,
+                               int r, int rpad, float* __restrict__ A, float* __restrict__ B,
+                               unsigned* __restrict__ colmax_bits) {
+  const int64_t total = d * rpad;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / rpad;
+    const int k = int(e - i * rpad);
+    double v = 0.0;
+    if (k < r)
+      v = v64 ? static_cast<const double*>(V)[i * ldv + k] : double(static_cast<const float*>(V)[i * ldv + k]);
+    const float b = float(v);
+    A[e] = k < r ? float(v * psi[k]) : 0.f;
+    B[e] = b;
+    if (k < r) atomicMax(&colmax_bits[k], __float_as_uint(fabsf(b)));
+  }
+}
+
+// FP32 screen.  Rows: rows[mi] for mi < m (m = *count_dev when count_dev is
+// set, else m_host), or mi itself when rows is NULL.  Writes, per listed row
+// position mi, cand_idx/cand_val [mi][kC] and thr[mi] (the kC-th screened
+// value, or -1 when the row saw fewer than kC columns).
+__global__ void __launch_bounds__(256) screen_fp32_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                                                          int64_t d, int rpad, const int* __restrict__ rows,
+                                                          int64_t m_host, const int* __restrict__ count_dev,
+                                                          int32_t* __restrict__ cand_idx,
+                                                          float* __restrict__ cand_val, float* __restrict__ thr) {
+  extern __shared__ float sm[];
+  float* As = sm;                   // [kBK][kBM + 1]
+  float* Bs = As + kBK * (kBM + 1); // [kBK][kBN + 1]
+  float* T = Bs + kBK * (kBN + 1);  // [kBM][kBN + 1]
+  float* lv = T + kBM * (kBN + 1);  // [kBM][kC]
+  int* li = reinterpret_cast<int*>(lv + kBM * kC);
+  __shared__ int64_t row_id[kBM];
+  const int64_t m_rows = count_dev ? int64_t(*count_dev) : m_host;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t nblk = (m_rows + kBM - 1) / kBM;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t m0 = blk * kBM;
+    for (int t = threadIdx.x; t < kBM; t += blockDim.x) {
+      const int64_t mi = m0 + t;
+      row_id[t] = mi < m_rows ? (rows ? int64_t(rows[mi]) : mi) : -1;
+    }
+    int cnt = 0, minpos = 0;
+    float minv = -1.f;
+    __syncthreads();
+    for (int64_t j0 = 0; j0 < d; j0 += kBN) {
+      float acc[8][4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int k0 = 0; k0 < rpad; k0 += kBK) {
+        for (int e = threadIdx.x; e < kBK * kBM; e += blockDim.x) {
+          const int rr = e / kBK, kk = e - rr * kBK;  // consecutive threads -> consecutive k
+          const int64_t gi = row_id[rr];
+          As[kk * (kBM + 1) + rr] = gi >= 0 ? A[gi * rpad + k0 + kk] : 0.f;
+        }
+        for (int e = threadIdx.x; e < kBK * kBN; e += blockDim.x) {
+          const int cc = e / kBK, kk = e - cc * kBK;
+          const int64_t gj = j0 + cc;
+          Bs[kk * (kBN + 1) + cc] = gj < d ? B[gj * rpad + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kBK; ++kk) {
+          float av[8], bv[4];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) av[a] = As[kk * (kBM + 1) + ty * 8 + a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = Bs[kk * (kBN + 1) + tx * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) T[(ty * 8 + a) * (kBN + 1) + tx * 4 + b] = acc[a][b];
+      __syncthreads();
+      if (threadIdx.x < kBM) {
+        const int t = threadIdx.x;
+        const int64_t gi = row_id[t];
+        if (gi >= 0) {
+          const int jn = d - j0 < kBN ? int(d - j0) : kBN;
+          for (int c = 0; c < jn; ++c) {
+            const int64_t j = j0 + c;
+            if (j == gi) continue;
+            const float v = fabsf(T[t * (kBN + 1) + c]);
+            list_offer(lv + t * kC, li + t * kC, cnt, minv, minpos, v, int(j));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x < kBM) {
+      const int t = threadIdx.x;
+      const int64_t mi = m0 + t;
+      if (mi < m_rows) {
+        for (int c = 0; c < kC; ++c) {
+          cand_idx[mi * kC + c] = c < cnt ? li[t * kC + c] : -1;
+          cand_val[mi * kC + c] = c < cnt ? lv[t * kC + c] : -1.f;
+        }
+        thr[mi] = cnt >= kC ? minv : -1.f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double vload(const void* V, int v64, int64_t idx) {
+  return v64 ? static_cast<const double*>(V)[idx] : double(static_cast<const float*>(V)[idx]);
+}
+
+__device__ __forceinline__ bool better(double a, int ja, double b, int jb) { return a > b || (a == b && ja < jb); }
+
+// One warp per listed row: exact FP64 values of the kC candidates, warp
+// bitonic sort (|value| desc, column asc), certification, output.
+__global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv, const double* __restrict__ psi,
+                               int k, const int* __restrict__ rows, int64_t m_host, const int* __restrict__ count_dev,
+                               const int32_t* __restrict__ cidx, const float* __restrict__ thr,
+                               const unsigned* __restrict__ colmax_bits, double u, int32_t* __restrict__ idx_out,
+                               float* __restrict__ val_out, int* __restrict__ flag_list,
+                               int* __restrict__ flag_count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t m = count_dev ? int64_t(*count_dev) : m_host;
+  const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t mi = w0; mi < m; mi += nw) {
+    const int64_t i = rows ? int64_t(rows[mi]) : mi;
+    const int j = cidx[mi * kC + lane];
+    double ex = 0.0;
+    if (j >= 0) {
+      for (int q = 0; q < r; ++q) ex += vload(V, v64, i * ldv + q) * psi[q] * vload(V, v64, int64_t(j) * ldv + q);
+    }
+    double key = j >= 0 ? fabs(ex) : -1.0;
+    int kj = j >= 0 ? j : INT_MAX;
+    double sv = ex;
+    for (int size = 2; size <= 32; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const double ok = __shfl_xor_sync(0xffffffffu, key, stride);
+        const int oj = __shfl_xor_sync(0xffffffffu, kj, stride);
+        const double os = __shfl_xor_sync(0xffffffffu, sv, stride);
+        const bool desc = (lane & size) == 0;
+        const bool lower = (lane & stride) == 0;
+        const bool take_better = lower == desc;
+        const bool self_better = better(key, kj, ok, oj);
+        if (take_better != self_better) key = ok, kj = oj, sv = os;
+      }
+    }
+    // error bound of the screen for this row
+    double bnd = 0.0;
+    for (int q = lane; q < r; q += 32)
+      bnd += fabs(vload(V, v64, i * ldv + q) * psi[q]) * double(__uint_as_float(colmax_bits[q]));
+    bnd = warp_sum(bnd) * u;
+    const double qk = __shfl_sync(0xffffffffu, key, k - 1);
+    const double t = double(thr[mi]);
+    const bool certified = t < 0.0 || qk > t + bnd;
+    if (lane < k) {
+      idx_out[i * k + lane] = kj == INT_MAX ? -1 : kj;
+      val_out[i * k + lane] = float(sv);
+    }
+    if (!certified && lane == 0) {
+      const int pos = atomicAdd(flag_count, 1);
+      flag_list[pos] = int(i);
+    }
+  }
+}
+
+constexpr int kExThreads = 256;
+
+// Exact FP64 scan of the listed rows, one CTA per row: per-thread sorted
+// top-k lists, then k rounds of a block-wide arg-best over the list heads.
+__global__ void __launch_bounds__(kExThreads) exact_rows_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv,
+                                                                 const double* __restrict__ psi, int k,
+                                                                 const int* __restrict__ rows,
+                                                                 const int* __restrict__ count_dev,
+                                                                 int32_t* __restrict__ idx_out,
+                                                                 float* __restrict__ val_out) {
+  extern __shared__ double esm[];
+  double* a = esm;                                       // [r]
+  double* lvv = a + r;                                   // [threads][k] signed values
+  int* lj = reinterpret_cast<int*>(lvv + kExThreads * k);  // [threads][k]
+  __shared__ double bkey[kExThreads];
+  __shared__ int bj[kExThreads];
+  __shared__ int bt[kExThreads];
+  const int m = *count_dev;
+  for (int mi = blockIdx.x; mi < m; mi += gridDim.x) {
+    const int64_t i = rows[mi];
+    for (int q = threadIdx.x; q < r; q += blockDim.x) a[q] = vload(V, v64, i * ldv + q) * psi[q];
+    __syncthreads();
+    double* mv = lvv + threadIdx.x * k;
+    int* mj = lj + threadIdx.x * k;
+    int cnt = 0;
+    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+      if (j == i) continue;
+      double ex = 0.0;
+      for (int q = 0; q < r; ++q) ex += a[q] * vload(V, v64, j * ldv + q);
+      const double ax = fabs(ex);
+      // sorted insertion (best first)
+      int pos = cnt < k ? cnt : k;
+      while (pos > 0 && better(ax, int(j), fabs(mv[pos - 1]), mj[pos - 1])) --pos;
+      if (pos < k) {
+        const int last = cnt < k ? cnt : k - 1;
+        for (int q = last; q > pos; --q) mv[q] = mv[q - 1], mj[q] = mj[q - 1];
+        mv[pos] = ex;
+        mj[pos] = int(j);
+        if (cnt < k) ++cnt;
+      }
+    }
+    int head = 0;
+    for (int out = 0; out < k; ++out) {
+      bkey[threadIdx.x] = head < cnt ? fabs(mv[head]) : -1.0;
+      bj[threadIdx.x] = head < cnt ? mj[head] : INT_MAX;
+      bt[threadIdx.x] = threadIdx.x;
+      __syncthreads();
+      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+          const int o = threadIdx.x + s;
+          if (better(bkey[o], bj[o], bkey[threadIdx.x], bj[threadIdx.x]))
+            bkey[threadIdx.x] = bkey[o], bj[threadIdx.x] = bj[o], bt[threadIdx.x] = bt[o];
+        }
+        __syncthreads();
+      }
+      const int win = bt[0];
+      if (threadIdx.x == win) {
+        idx_out[i * k + out] = head < cnt ? mj[head] : -1;
+        val_out[i * k + out] = head < cnt ? float(mv[head]) : 0.f;
+        ++head;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+double screen_unit(gmgm_prec prec, int r) {
+  const double u32 = 1.0 / 16777216.0;  // 2^-24
+  const double kf = 1.02;               // slack over the first-order bound
+  const double acc = (double(r) + 4.0) * u32;
+  if (prec == GMGM_FP32) return kf * acc;
+  if (prec == GMGM_BF16) return kf * (2.0 / 256.0 + acc);
+  return kf * (6.0 / 65536.0 + acc);  // BF16X3: dropped lo*lo and rounding of lo
+}
+
+void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
+                    const int* rows, const int* count_dev, const int32_t* cidx, const float* /*cval*/,
+                    const float* thr, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
+                    int* flag_list, int* flag_count) {
+  const int64_t m = rows ? d : d;  // grid covers d rows at most
+  const unsigned blocks = unsigned(std::min<int64_t>((m * 32 + 255) / 256, 65536));
+  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, thr, colmax_bits, u,
+                                        idx, val, flag_list, flag_count);
+}
+
+void launch_exact_rows(cudaStream_t s, int num_sms, int64_t d, int r, const void* V, int v64, int64_t ldv,
+                       const double* psi, int k, const int* rows, const int* count_dev, int32_t* idx, float* val) {
+  const size_t smem = size_t(r) * 8 + size_t(kExThreads) * k * 12;
+  cudaFuncSetAttribute(exact_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  exact_rows_kernel<<<unsigned(num_sms) * 2, kExThreads, smem, s>>>(d, r, V, v64, ldv, psi, k, rows, count_dev, idx,
+                                                                   val);
+}
+
+size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
+  const int64_t rpad = ((r + kBK - 1) / kBK) * kBK;
+  size_t b = 0;
+  b += Carve::round(size_t(d) * rpad * 4) * 2;  // A, B
+  b += Carve::round(size_t(r) * 4);             // colmax
+  b += Carve::round(size_t(d) * kC * 4) * 2;    // level-1 candidates
+  b += Carve::round(size_t(d) * 4);             // level-1 thr
+  b += Carve::round(size_t(d) * 4) * 2;         // flag lists
+  b += Carve::round(size_t(d) * kC * 4) * 2;    // level-2 candidates
+  b += Carve::round(size_t(d) * 4);             // level-2 thr
+  b += Carve::round(64);                        // counters
+  b += Carve::round(topk_tc_scratch_bytes(d, r, prec));
+  return b + 4096;
+}
+
+int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv, const double* psi,
+             int32_t k, gmgm_prec prec, int32_t* idx, float* val, void* scratch, gmgm_topk_stats* st) {
+  cudaStream_t s = h->stream;
+  const int rpad = ((r + kBK - 1) / kBK) * kBK;
+  Carve c(scratch);
+  float* A = c.take<float>(size_t(d) * rpad);
+  float* B = c.take<float>(size_t(d) * rpad);
+  unsigned* colmax = c.take<unsigned>(r);
+  int32_t* cidx = c.take<int32_t>(size_t(d) * kC);
+  float* cval = c.take<float>(size_t(d) * kC);
+  float* thr = c.take<float>(d);
+  int* flag1 = c.take<int>(d);
+  int* flag2 = c.take<int>(d);
+  int32_t* cidx2 = c.take<int32_t>(size_t(d) * kC);
+  float* cval2 = c.take<float>(size_t(d) * kC);
+  float* thr2 = c.take<float>(d);
+  int* counters = c.take<int>(16);
+  void* tc_scratch = c.take<char>(topk_tc_scratch_bytes(d, r, prec));
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  if (st)
+    for (auto& e : ev) cudaEventCreate(&e);
+  GMGM_CUDA_TRY(h, cudaMemsetAsync(colmax, 0, size_t(r) * 4, s));
+  GMGM_CUDA_TRY(h, cudaMemsetAsync(counters, 0, 64, s));
+  {
+    const int64_t total = d * rpad;
+    const unsigned blocks = unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 16));
+    prep_ab_kernel<<<blocks, 256, 0, s>>>(V, v_fp64, ldv, psi, d, r, rpad, A, B, colmax);
+  }
+  if (st) cudaEventRecord(ev[0], s);
+  const size_t smem = size_t(kBK * (kBM + 1) + kBK * (kBN + 1) + kBM * (kBN + 1) + kBM * kC) * 4 + size_t(kBM * kC) * 4;
+  GMGM_CUDA_TRY(h, cudaFuncSetAttribute(screen_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const unsigned sblocks = unsigned(std::min<int64_t>((d + kBM - 1) / kBM, int64_t(h->num_sms) * 2));
+  if (prec == GMGM_FP32) {
+    screen_fp32_kernel<<<sblocks, 256, smem, s>>>(A, B, d, rpad, nullptr, d, nullptr, cidx, cval, thr);
+  } else {
+    GMGM_CUDA_TRY(h, launch_screen_tc(h, d, r, V, v_fp64, ldv, psi, prec, cidx, cval, thr, tc_scratch));
+  }
+  if (st) cudaEventRecord(ev[1], s);
+  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, colmax, screen_unit(prec, r),
+                 idx, val, flag1, counters + 0);
+  const int* lvl3 = flag1;
+  const int* lvl3_count = counters + 0;
+  if (prec != GMGM_FP32) {
+    screen_fp32_kernel<<<unsigned(h->num_sms) * 2, 256, smem, s>>>(A, B, d, rpad, flag1, 0, counters + 0, cidx2,
+                                                                   cval2, thr2);
+    launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, flag1, counters + 0, cidx2, cval2, thr2, colmax,
+                   screen_unit(GMGM_FP32, r), idx, val, flag2, counters + 1);
+    lvl3 = flag2;
+    lvl3_count = counters + 1;
+  }
+  launch_exact_rows(s, h->num_sms, d, r, V, v_fp64, ldv, psi, k, lvl3, lvl3_count, idx, val);
+  if (st) cudaEventRecord(ev[2], s);
+  GMGM_CUDA_TRY(h, cudaGetLastError());
+  if (st) {
+    int hc[2] = {0, 0};
+    GMGM_CUDA_TRY(h, cudaMemcpyAsync(hc, counters, 8, cudaMemcpyDeviceToHost, s));
+    GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
+    float t1 = 0.f, t2 = 0.f;
+    cudaEventElapsedTime(&t1, ev[0], ev[1]);
+    cudaEventElapsedTime(&t2, ev[1], ev[2]);
+    st->rows_uncertified = hc[0];
+    st->candidates = kC;
+    st->screen_ms = t1;
+    st->rescore_ms = t2;
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  return GMGM_OK;
+}
+
+}  // namespace gmgm

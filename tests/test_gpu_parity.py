@@ -1,0 +1,270 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle on the same
+seeded inputs (sizes that span several tiles and a ragged tail)."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import gram as og
+from oracle import recon as orc
+from oracle import solve as osv
+from oracle import spectra as osp
+from synth import planted_c1, scrna_counts
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g(cuda_dev):
+    import paper_2407_19892_gb300 as pkg
+    from paper_2407_19892_gb300 import build
+    build.build()
+    return pkg
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ---- preprocessing ---------------------------------------------------------
+
+@pytest.mark.parametrize("n,p", [(1000, 130), (4097, 64), (2, 1)])
+def test_preprocess_matches_oracle(g, cuda_dev, n, p):
+    counts = scrna_counts(n, max(p, 2), 5, seed=11)[:, :p].contiguous()
+    x, hi, lo, ld_t = g.preprocess(counts.to(cuda_dev), split=True)
+    ref = og.log1p_centre(counts.numpy())
+    np.testing.assert_allclose(x.cpu().numpy(), ref, atol=2e-6 * max(1.0, np.abs(ref).max()))
+    xt = (hi.float() + lo.float()).cpu().numpy()
+    assert xt.shape == (p, ld_t) and ld_t % 64 == 0
+    np.testing.assert_allclose(xt[:, :n], x.cpu().numpy().T, atol=1e-4 * max(1.0, np.abs(ref).max()))
+    assert np.all(xt[:, n:] == 0)
+
+
+# ---- Gram ------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,p", [(5000, 200), (777, 65), (64, 1)])
+def test_gram_fp32_cols(g, cuda_dev, n, p):
+    x = _rng(1).standard_normal((n, p)).astype(np.float32)
+    S = g.gram(torch.from_numpy(x).to(cuda_dev), g.SIDE_COLS, g.FP32).cpu().numpy()
+    ref = og.gram(x.astype(np.float64), 1)
+    assert np.max(np.abs(S - ref)) <= 2e-6 * np.abs(ref).max()
+    assert np.array_equal(S, S.T)
+
+
+def test_gram_rows_and_tensor_axes(g, cuda_dev):
+    t = _rng(2).standard_normal((7, 40, 33)).astype(np.float32)
+    tt = torch.from_numpy(t).to(cuda_dev)
+    s0 = g.gram(tt.reshape(7, 40 * 33), g.SIDE_ROWS, g.FP32).cpu().numpy()
+    s1 = g.gram(tt, g.SIDE_ROWS, g.FP32).cpu().numpy()           # batch of 40 x 33 slices
+    s2 = g.gram(tt.reshape(7 * 40, 33), g.SIDE_COLS, g.FP32).cpu().numpy()
+    for ax, s in enumerate((s0, s1, s2)):
+        ref = og.gram(t.astype(np.float64), ax)
+        assert np.max(np.abs(s - ref)) <= 2e-6 * np.abs(ref).max(), ax
+
+
+def test_gram_accumulate_is_multimodal_sum(g, cuda_dev):
+    r = _rng(3)
+    x1 = r.standard_normal((300, 50)).astype(np.float32)
+    x2 = r.standard_normal((300, 70)).astype(np.float32)
+    S = g.gram(torch.from_numpy(x1).to(cuda_dev), g.SIDE_ROWS, g.FP32)
+    g.gram(torch.from_numpy(x2).to(cuda_dev), g.SIDE_ROWS, g.FP32, out=S, accumulate=True)
+    ref = og.gram_multimodal([x1.astype(np.float64), x2.astype(np.float64)], [("c", "g"), ("c", "p")], "c")
+    assert np.max(np.abs(S.cpu().numpy() - ref)) <= 2e-6 * np.abs(ref).max()
+
+
+# ---- spectra -----------------------------------------------------------------
+
+def _check_eig(S, ev, W, r):
+    e_ref, w_ref = osp.top_eigh(S, r)
+    scale = np.abs(e_ref).max()
+    np.testing.assert_allclose(ev, e_ref, rtol=0, atol=1e-11 * scale)
+    if W is not None:
+        res = S @ W - W * ev[None, :]
+        assert np.max(np.abs(res)) <= 1e-10 * scale
+        assert np.max(np.abs(W.T @ W - np.eye(r))) <= 1e-8
+
+
+@pytest.mark.parametrize("d,r", [(300, 300), (257, 17), (3, 3), (2, 1), (1, 1), (1000, 1000)])
+def test_spectra_random_gram(g, cuda_dev, d, r):
+    x = _rng(4).standard_normal((d + 50, d))
+    S = x.T @ x
+    ev, W = g.spectra(torch.from_numpy(S).to(cuda_dev), r)
+    _check_eig(S, ev.cpu().numpy(), W.cpu().numpy(), r)
+
+
+def test_spectra_degenerate_and_clustered(g, cuda_dev):
+    # identity (one eigenvalue of multiplicity d) and a block of near-equal values
+    d = 120
+    S = np.eye(d) * 3.0
+    ev, W = g.spectra(torch.from_numpy(S).to(cuda_dev), 40)
+    _check_eig(S, ev.cpu().numpy(), W.cpu().numpy(), 40)
+    q, _ = np.linalg.qr(_rng(5).standard_normal((d, d)))
+    lam = np.linspace(1.0, 2.0, d)
+    lam[:10] = 5.0 + 1e-13 * np.arange(10)
+    S = (q * lam) @ q.T
+    S = 0.5 * (S + S.T)
+    ev, W = g.spectra(torch.from_numpy(S).to(cuda_dev), 30)
+    _check_eig(S, ev.cpu().numpy(), W.cpu().numpy(), 30)
+
+
+def test_lift_matches_oracle(g, cuda_dev):
+    x, _, _ = planted_c1()
+    x = (x - x.mean(0)).astype(np.float32)
+    S = og.gram(x.astype(np.float64), 1)
+    e, w = osp.top_eigh(S, 37)
+    U = g.lift(torch.from_numpy(x).to(cuda_dev), torch.from_numpy(w).to(cuda_dev),
+               torch.from_numpy(e).to(cuda_dev), 37).cpu().numpy()
+    ref = osp.dual_lift(x.astype(np.float64), w, e)
+    assert np.max(np.abs(U - ref)) <= 1e-5 * np.abs(ref).max()
+
+
+# ---- eigenvalue solve ------------------------------------------------------------
+
+def _sums(lams, mods):
+    out = []
+    for m in mods:
+        s = osv.grid([np.asarray(l) for l in lams], m)
+        out.append(np.asarray(s).ravel())
+    return np.concatenate(out)
+
+
+def _solve_case(g, cuda_dev, E, mods, tol=1e-9):
+    prob = osv.KSProblem(E, mods)
+    ref, info = osv.solve_newton(prob)
+    lams, st = g.eigsolve([torch.from_numpy(e).to(cuda_dev) for e in E], mods, tol=tol)
+    got = [l.cpu().numpy() for l in lams]
+    assert st["status"] == 0, st
+    assert st["rel_kkt"] <= 10 * tol, st
+    a = _sums(got, mods)
+    b = _sums(prob.split(ref), mods)
+    err = np.max(np.abs(a - b) / np.abs(b))
+    return err, st, got, prob
+
+
+def test_eigsolve_full_rank_gauge(g, cuda_dev):
+    x, _, _ = planted_c1()
+    e_r, _, e_c, _ = osp.two_axis_spectra(x, 100, 100)
+    err, st, got, prob = _solve_case(g, cuda_dev, [e_r, e_c], [(0, 1)])
+    assert err <= 1e-7, err
+    # gauge convention: min of the second axis at eps
+    assert abs(got[1].min() - prob.eps[1]) <= 1e-12 * got[0].max()
+
+
+@pytest.mark.parametrize("r1", [1, 10, 37])
+def test_eigsolve_truncated_box(g, cuda_dev, r1):
+    x, _, _ = planted_c1()
+    e_r, _, e_c, _ = osp.two_axis_spectra(x, r1, 100)
+    err, st, got, prob = _solve_case(g, cuda_dev, [e_r, e_c], [(0, 1)])
+    assert err <= 1e-7, err
+    assert st["n_active"] > 0
+
+
+def test_eigsolve_scrna_like_spectrum(g, cuda_dev):
+    counts = scrna_counts(4000, 300, 8, seed=21)
+    x = og.log1p_centre(counts.numpy())
+    e_all, _ = osp.top_eigh(x.T @ x, 300)
+    err, st, _, _ = _solve_case(g, cuda_dev, [e_all[:40], e_all], [(0, 1)])
+    assert err <= 1e-7, err
+
+
+def test_eigsolve_three_axis_and_multimodal(g, cuda_dev):
+    r = _rng(6)
+    t = r.standard_normal((5, 7, 6))
+    es = [osp.top_eigh(og.gram(t, a), t.shape[a])[0] for a in range(3)]
+    err, st, _, _ = _solve_case(g, cuda_dev, es, [(0, 1, 2)])
+    assert err <= 1e-7, err
+    # two modalities sharing axis 0 (cells x genes, cells x peaks), truncated cells
+    x1 = r.standard_normal((60, 20))
+    x2 = r.standard_normal((60, 30))
+    sc = og.gram_multimodal([x1, x2], [("c", "g"), ("c", "p")], "c")
+    e_c = osp.top_eigh(sc, 15)[0]
+    e_g = osp.top_eigh(x1.T @ x1, 20)[0]
+    e_p = osp.top_eigh(x2.T @ x2, 30)[0]
+    err, st, _, _ = _solve_case(g, cuda_dev, [e_c, e_g, e_p], [(0, 1), (0, 2)])
+    assert err <= 1e-7, err
+
+
+def test_eigsolve_warm_start_and_fp64_only(g, cuda_dev):
+    x, _, _ = planted_c1()
+    e_r, _, e_c, _ = osp.two_axis_spectra(x, 20, 100)
+    E = [torch.from_numpy(e).to(cuda_dev) for e in (e_r, e_c)]
+    lams, st = g.eigsolve(E, [(0, 1)], tol=1e-10, fp32_phase=False)
+    assert st["status"] == 0 and st["rel_kkt"] <= 1e-9
+    lams2, st2 = g.eigsolve(E, [(0, 1)], tol=1e-10, init=lams)
+    assert st2["newton_iters"] <= 1
+    for a, b in zip(lams, lams2):
+        torch.testing.assert_close(a, b, rtol=1e-8, atol=0)
+
+
+# ---- top-k ------------------------------------------------------------------------
+
+def _check_topk(V64, lam, k, idx, val):
+    """Stage-wise parity: the oracle's FP64 top-k of the same V, psi."""
+    ref_i, ref_v = orc.topk_rows(V64, lam, k)
+    gap = orc.topk_gap(V64, lam, k)
+    ok = gap > 1e-5
+    assert np.array_equal(np.sort(idx[ok], 1), np.sort(ref_i[ok], 1))
+    # order inside the list follows the exact values
+    mag = np.abs(ref_v[ok])
+    distinct = np.all(np.diff(mag, axis=1) < -1e-12 * mag[:, :1], axis=1)
+    assert np.array_equal(idx[ok][distinct], ref_i[ok][distinct])
+    np.testing.assert_allclose(np.take_along_axis(val, np.argsort(idx, 1), 1)[ok],
+                               np.take_along_axis(ref_v, np.argsort(ref_i, 1), 1)[ok].astype(np.float32),
+                               rtol=1e-6, atol=1e-30)
+    return ok.mean()
+
+
+@pytest.mark.parametrize("d,r,k", [(1000, 50, 10), (517, 7, 32), (40, 3, 5), (20, 64, 19), (300, 200, 20)])
+def test_topk_fp32_random(g, cuda_dev, d, r, k):
+    rng = _rng(7 + d)
+    V = rng.standard_normal((d, r)).astype(np.float32)
+    lam = rng.uniform(0.1, 2.0, r)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(lam).to(cuda_dev), k)
+    frac = _check_topk(V.astype(np.float64), lam, k, idx.cpu().numpy(), val.cpu().numpy())
+    assert frac > 0.9
+
+
+def test_topk_fp64_input_and_ties(g, cuda_dev):
+    # duplicate rows give exact ties: lower column index first
+    rng = _rng(8)
+    base = rng.standard_normal((50, 6))
+    V = np.repeat(base, 3, axis=0)
+    lam = rng.uniform(0.5, 1.5, 6)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(lam).to(cuda_dev), 4)
+    ref_i, ref_v = orc.topk_rows(V, lam, 4)
+    assert np.array_equal(idx.cpu().numpy(), ref_i)
+    np.testing.assert_allclose(val.cpu().numpy(), ref_v.astype(np.float32), rtol=1e-6)
+
+
+def test_topk_identity_all_zero_ties(g, cuda_dev):
+    V = np.eye(40)
+    lam = np.ones(40)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(lam).to(cuda_dev), 3)
+    ref_i, _ = orc.topk_rows(V, lam, 3)
+    assert np.array_equal(idx.cpu().numpy(), ref_i)
+    assert st["rows_uncertified"] == 40
+
+
+def test_topk_argument_errors(g, cuda_dev):
+    V = torch.zeros(10, 3, device=cuda_dev)
+    psi = torch.ones(3, dtype=torch.float64, device=cuda_dev)
+    with pytest.raises(g.GmgmError):
+        g.topk_network(V, psi, 10)      # k >= d
+    with pytest.raises(g.GmgmError):
+        g.topk_network(V, psi, 33)      # k > 32
+
+
+# ---- whole two-axis fit ---------------------------------------------------------------
+
+def test_fit_two_axis_c1(g, cuda_dev):
+    from oracle.fit import fit_two_axis as ofit
+    x, _, _ = planted_c1()
+    x = (x - x.mean(0)).astype(np.float32)
+    res = g.fit_two_axis(torch.from_numpy(x).to(cuda_dev), 30, 100, 10, 10)
+    ref = ofit(x.astype(np.float64), 30, 100, 10, 10)
+    sg = res.lam_rows.cpu().numpy()[:, None] + res.lam_cols.cpu().numpy()[None, :]
+    sr = ref.lam_rows[:, None] + ref.lam_cols[None, :]
+    assert np.max(np.abs(sg - sr) / sr) <= 1e-4
+    for V, lam, k, idx, val in ((res.v_rows, res.lam_rows, 10, res.idx_rows, res.val_rows),
+                                (res.v_cols, res.lam_cols, 10, res.idx_cols, res.val_cols)):
+        _check_topk(V.double().cpu().numpy(), lam.cpu().numpy(), k, idx.cpu().numpy(), val.cpu().numpy())
