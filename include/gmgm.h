@@ -101,6 +101,10 @@ int gmgm_device_status(gmgm_handle* h);
 /* Library version string, e.g. "gmgm 0.1 sm_103a". */
 const char* gmgm_version(void);
 
+/* Number of CUDA kernels this library has launched in this process, over
+ * all handles (a diagnostic for benchmarks; not synchronising). */
+uint64_t gmgm_kernel_launches(void);
+
 /* ---- preprocessing ------------------------------------------------------ */
 
 /* X = log1p(counts) - column means, for an n x p count matrix (cells x genes).

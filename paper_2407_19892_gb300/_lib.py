@@ -67,6 +67,7 @@ SIGNATURES = {
     "gmgm_last_error": (ctypes.c_char_p, [c_vp]),
     "gmgm_device_status": (c_int, [c_vp]),
     "gmgm_version": (ctypes.c_char_p, []),
+    "gmgm_kernel_launches": (ctypes.c_uint64, []),
     "gmgm_preprocess": (c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp,
                                 c_i64, c_vp]),
     "gmgm_gram": (c_int, [c_vp, ctypes.POINTER(Matrix), c_int, c_int, c_vp, c_i64, c_int]),

@@ -155,6 +155,8 @@ def spectra(S: torch.Tensor, r: int, vectors: bool = True, h: Handle = None):
     """Top-r eigenpairs (descending) of a symmetric FP64 matrix on the GPU."""
     h = h or handle(S.device)
     _need_cuda(S, torch.float64, "S")
+    if S.stride(1) != 1:
+        S = S.contiguous()
     d = S.shape[0]
     ev = torch.empty(r, dtype=torch.float64, device=S.device)
     W = torch.empty(d, r, dtype=torch.float64, device=S.device) if vectors else None
@@ -166,6 +168,8 @@ def lift(x: torch.Tensor, W: torch.Tensor, E: torch.Tensor, r: int, h: Handle = 
     """U = X W_r diag(E_r)^-1/2 (rows x r, FP32)."""
     h = h or handle(x.device)
     _need_cuda(x, torch.float32, "x")
+    W = W.contiguous()
+    E = E.contiguous()
     m = _matrix(x)
     U = torch.empty(x.shape[0], r, dtype=torch.float32, device=x.device)
     h.check(h.lib.gmgm_lift(h.h, ctypes.byref(m), r, _ptr(W), W.stride(0), _ptr(E), _ptr(U), r))
@@ -217,8 +221,10 @@ def topk_network(V: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32,
     """Per-row top-k of |V diag(psi) V^T| (diagonal excluded).  Returns
     (idx int32 [d, k], val float32 [d, k], stats dict)."""
     h = h or handle(V.device)
-    if V.dtype not in (torch.float32, torch.float64) or not V.is_cuda or V.stride(1) != 1:
-        raise ValueError("V must be a row-major CUDA FP32/FP64 matrix")
+    if V.dtype not in (torch.float32, torch.float64) or not V.is_cuda:
+        raise ValueError("V must be a CUDA FP32/FP64 matrix")
+    if V.stride(1) != 1:
+        V = V.contiguous()
     _need_cuda(psi, torch.float64, "psi")
     d, r = V.shape
     idx = torch.empty(d, k, dtype=torch.int32, device=V.device)

@@ -1,6 +1,7 @@
 // C-ABI entry points: argument checks, scratch management and dispatch.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -12,6 +13,10 @@ int fail(gmgm_handle* h, int code, const std::string& msg) {
   if (h) h->last_error = msg;
   return code;
 }
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch(int n) { g_launches.fetch_add(static_cast<unsigned long long>(n), std::memory_order_relaxed); }
 
 int ensure_scratch(gmgm_handle* h, size_t bytes) {
   if (bytes <= h->scratch_bytes) return GMGM_OK;
@@ -38,6 +43,8 @@ using gmgm::fail;
 extern "C" {
 
 const char* gmgm_version(void) { return "gmgm 0.1 sm_103a"; }
+
+uint64_t gmgm_kernel_launches(void) { return gmgm::g_launches.load(std::memory_order_relaxed); }
 
 int gmgm_create(gmgm_handle** out, int device, void* stream) {
   if (!out) return GMGM_E_ARG;
@@ -183,7 +190,7 @@ int gmgm_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const double* W, 
   if (r < 1 || r > 256 || r > m->cols || !W || !E || !U || ldw < r || ldu < r)
     return fail(h, GMGM_E_ARG, "gmgm_lift: need 1 <= r <= min(256, cols), ldw, ldu >= r");
   GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
-  int rc = gmgm::ensure_scratch(h, size_t(m->cols) * r * sizeof(float) + 256);
+  int rc = gmgm::ensure_scratch(h, size_t(m->cols) * ((r + 63) / 64) * 64 * sizeof(float) + 256);
   if (rc) return rc;
   GMGM_CUDA_TRY(h, gmgm::launch_lift(h, m, r, W, ldw, E, U, ldu, static_cast<float*>(h->scratch)));
   return GMGM_OK;

@@ -26,6 +26,9 @@ namespace gmgm {
 // Set the handle's message and return `code`.
 int fail(gmgm_handle* h, int code, const std::string& msg);
 
+// Count kernel launches issued by the library (process-wide diagnostic).
+void note_launch(int n = 1);
+
 // Ensure the scratch arena holds at least `bytes`; returns GMGM_OK or an
 // error (the arena is synchronised and re-allocated when it grows).
 int ensure_scratch(gmgm_handle* h, size_t bytes);

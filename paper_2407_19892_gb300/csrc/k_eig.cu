@@ -468,6 +468,7 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
     dim3 b(32, 8), g(unsigned((r + 31) / 32), unsigned((n + 31) / 32));
     output_kernel<<<g, b, 0, st>>>(s.lam, s.Zc, n, r, evals, evecs, ldv);
   }
+  note_launch(6 + 2 * ((r + B - 1) / B) + (evecs ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -164,6 +164,7 @@ cudaError_t launch_gram_fp32(gmgm_handle* h, const gmgm_matrix* m, int side, dou
   gram_fp32_kernel<<<grid, 256, 0, h->stream>>>(v, kps, tiles, partials);
   dim3 cb(32, 8), cg(unsigned((v.dS + 31) / 32), unsigned((v.dS + 7) / 8));
   gram_combine_kernel<<<cg, cb, 0, h->stream>>>(partials, splits, v.dS, S, lds, accumulate);
+  note_launch(3);
   return cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ cudaError_t launch_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const d
     else
       lift_kernel<64><<<blocks, kRows, 0, h->stream>>>(m->x, n, p, m->ld, wscr, rpad, c0, r, U, ldu);
   }
+  note_launch(1 + (r + RC - 1) / RC);
   return cudaGetLastError();
 }
 

@@ -112,6 +112,7 @@ cudaError_t launch_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float*
                                            reinterpret_cast<__nv_bfloat16*>(xt_lo), n, p, ld_t);
   }
   if (colmean_out) colmean_kernel<<<unsigned((p + 255) / 256), 256, 0, s>>>(colsum, n, p, colmean_out);
+  note_launch(2 + (xt_hi && ld_t > n ? 1 : 0) + (colmean_out ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -569,6 +569,7 @@ cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* co
   cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   solve_kernel<<<1, kThreads, smem, h->stream>>>(P, V, h->d_status, d_stats);
+  note_launch(1);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,21 @@ __global__ void prep_ab_kernel(const void* V, int v64, int64_t ldv, const double
   }
 }
 
+// max_j ||B_j||_2 over all rows (float bits, atomicMax), for the
+// Cauchy-Schwarz form of the screen's error bound.
+__global__ void rownorm_kernel(const float* __restrict__ B, int64_t d, int rpad, unsigned* __restrict__ maxrow_bits) {
+  float best = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < d; i += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < rpad; ++k) s = fmaf(B[i * rpad + k], B[i * rpad + k], s);
+    best = fmaxf(best, s);
+  }
+  // round the norm up so the bound stays an upper bound
+  best = sqrtf(best) * (1.f + 1.2e-7f * float(rpad + 8));
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxrow_bits, __float_as_uint(best));
+}
+
 // FP32 screen.  Rows: rows[mi] for mi < m (m = *count_dev when count_dev is
 // set, else m_host), or mi itself when rows is NULL.  Writes, per listed row
 // position mi, cand_idx/cand_val [mi][kC] and thr[mi] (the kC-th screened
@@ -182,10 +197,17 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
       }
     }
     // error bound of the screen for this row
-    double bnd = 0.0;
-    for (int q = lane; q < r; q += 32)
-      bnd += fabs(vload(V, v64, i * ldv + q) * psi[q]) * double(__uint_as_float(colmax_bits[q]));
-    bnd = warp_sum(bnd) * u;
+    // (sum_k |a_ik| max_j |b_jk|, or ||a_i|| max_j ||b_j|| by Cauchy-Schwarz;
+    // colmax_bits[r] holds max_j ||b_j||)
+    double bnd = 0.0, nrm = 0.0;
+    for (int q = lane; q < r; q += 32) {
+      const double aq = vload(V, v64, i * ldv + q) * psi[q];
+      bnd += fabs(aq) * double(__uint_as_float(colmax_bits[q]));
+      nrm += aq * aq;
+    }
+    bnd = warp_sum(bnd);
+    nrm = sqrt(warp_sum(nrm)) * (1.0 + 1e-12);
+    bnd = fmin(bnd, nrm * double(__uint_as_float(colmax_bits[r]))) * u;
     const double qk = __shfl_sync(0xffffffffu, key, k - 1);
     const double t = double(thr[mi]);
     const bool certified = t < 0.0 || qk > t + bnd;
@@ -271,10 +293,14 @@ __global__ void __launch_bounds__(kExThreads) exact_rows_kernel(int64_t d, int r
 double screen_unit(gmgm_prec prec, int r) {
   const double u32 = 1.0 / 16777216.0;  // 2^-24
   const double kf = 1.02;               // slack over the first-order bound
-  const double acc = (double(r) + 4.0) * u32;
-  if (prec == GMGM_FP32) return kf * acc;
-  if (prec == GMGM_BF16) return kf * (2.0 / 256.0 + acc);
-  return kf * (6.0 / 65536.0 + acc);  // BF16X3: dropped lo*lo and rounding of lo
+  // FP32 SIMT: operand rounding (2u) + FMA accumulation of r terms (r u).
+  // Tensor cores: operand rounding to BF16 (hi only: 2 * 2^-9; split: the
+  // dropped lo*lo and rounding of lo, 3 * 2^-18) + an accumulation of K
+  // products whose additions are each charged 2u (the tensor core's internal
+  // alignment/rounding is not IEEE round-to-nearest).
+  if (prec == GMGM_FP32) return kf * (double(r) + 4.0) * u32;
+  if (prec == GMGM_BF16) return kf * (2.0 / 512.0 + 2.0 * (double(r) + 4.0) * u32);
+  return kf * (3.0 / 262144.0 + 2.0 * (3.0 * double(r) + 4.0) * u32);
 }
 
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
@@ -299,7 +325,7 @@ size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
   const int64_t rpad = ((r + kBK - 1) / kBK) * kBK;
   size_t b = 0;
   b += Carve::round(size_t(d) * rpad * 4) * 2;  // A, B
-  b += Carve::round(size_t(r) * 4);             // colmax
+  b += Carve::round(size_t(r + 1) * 4);         // colmax + max row norm
   b += Carve::round(size_t(d) * kC * 4) * 2;    // level-1 candidates
   b += Carve::round(size_t(d) * 4);             // level-1 thr
   b += Carve::round(size_t(d) * 4) * 2;         // flag lists
@@ -317,7 +343,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   Carve c(scratch);
   float* A = c.take<float>(size_t(d) * rpad);
   float* B = c.take<float>(size_t(d) * rpad);
-  unsigned* colmax = c.take<unsigned>(r);
+  unsigned* colmax = c.take<unsigned>(r + 1);  // [r] = max row norm
   int32_t* cidx = c.take<int32_t>(size_t(d) * kC);
   float* cval = c.take<float>(size_t(d) * kC);
   float* thr = c.take<float>(d);
@@ -331,12 +357,14 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (st)
     for (auto& e : ev) cudaEventCreate(&e);
-  GMGM_CUDA_TRY(h, cudaMemsetAsync(colmax, 0, size_t(r) * 4, s));
+  GMGM_CUDA_TRY(h, cudaMemsetAsync(colmax, 0, size_t(r + 1) * 4, s));
   GMGM_CUDA_TRY(h, cudaMemsetAsync(counters, 0, 64, s));
   {
     const int64_t total = d * rpad;
     const unsigned blocks = unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 16));
     prep_ab_kernel<<<blocks, 256, 0, s>>>(V, v_fp64, ldv, psi, d, r, rpad, A, B, colmax);
+    const unsigned nb = unsigned(std::min<int64_t>((d + 255) / 256, int64_t(h->num_sms) * 8));
+    rownorm_kernel<<<nb, 256, 0, s>>>(B, d, rpad, colmax + r);
   }
   if (st) cudaEventRecord(ev[0], s);
   const size_t smem = size_t(kBK * (kBM + 1) + kBK * (kBN + 1) + kBM * (kBN + 1) + kBM * kC) * 4 + size_t(kBM * kC) * 4;
@@ -361,6 +389,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     lvl3_count = counters + 1;
   }
   launch_exact_rows(s, h->num_sms, d, r, V, v_fp64, ldv, psi, k, lvl3, lvl3_count, idx, val);
+  note_launch(prec == GMGM_FP32 ? 5 : 6);
   if (st) cudaEventRecord(ev[2], s);
   GMGM_CUDA_TRY(h, cudaGetLastError());
   if (st) {
