@@ -252,11 +252,13 @@ int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p,
 /* ---- step 4: recomposition + per-row top-k ------------------------------ */
 
 typedef struct {
-  int64_t rows_uncertified;  /* rows whose screen margin did not certify the
-                                top-k and that were recomputed exactly */
+  int64_t rows_uncertified;  /* rows the first screen did not certify */
+  int64_t rows_exact;        /* rows that ended in the exact FP64 scan */
   int64_t candidates;        /* candidate slots per row used by the screen */
-  double screen_ms;          /* device time of the screen kernel */
+  double screen_ms;          /* device time of the first screen */
   double rescore_ms;         /* device time of rescoring (+ repair) */
+  double screen_err_ratio;   /* max over candidates of |screened - exact| /
+                                the screen's error bound (<= 1 expected) */
 } gmgm_topk_stats;
 
 /* Per-row top-k of Psi = V diag(psi) V^T without forming Psi (Algorithm 1:

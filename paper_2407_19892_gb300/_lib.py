@@ -52,8 +52,8 @@ class SolveStats(ctypes.Structure):
 
 
 class TopkStats(ctypes.Structure):
-    _fields_ = [("rows_uncertified", c_i64), ("candidates", c_i64),
-                ("screen_ms", c_dbl), ("rescore_ms", c_dbl)]
+    _fields_ = [("rows_uncertified", c_i64), ("rows_exact", c_i64), ("candidates", c_i64),
+                ("screen_ms", c_dbl), ("rescore_ms", c_dbl), ("screen_err_ratio", c_dbl)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

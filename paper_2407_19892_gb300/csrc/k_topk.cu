@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <cstring>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -166,10 +167,11 @@ __device__ __forceinline__ bool better(double a, int ja, double b, int jb) { ret
 // bitonic sort (|value| desc, column asc), certification, output.
 __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv, const double* __restrict__ psi,
                                int k, const int* __restrict__ rows, int64_t m_host, const int* __restrict__ count_dev,
-                               const int32_t* __restrict__ cidx, const float* __restrict__ thr,
-                               const unsigned* __restrict__ colmax_bits, double u, int32_t* __restrict__ idx_out,
-                               float* __restrict__ val_out, int* __restrict__ flag_list,
-                               int* __restrict__ flag_count) {
+                               const int32_t* __restrict__ cidx, const float* __restrict__ cval,
+                               const float* __restrict__ thr, const unsigned* __restrict__ colmax_bits, double u,
+                               int32_t* __restrict__ idx_out, float* __restrict__ val_out,
+                               int* __restrict__ flag_list, int* __restrict__ flag_count,
+                               unsigned* __restrict__ err_bits) {
   const int lane = threadIdx.x & 31;
   const int64_t m = count_dev ? int64_t(*count_dev) : m_host;
   const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -181,6 +183,8 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
     if (j >= 0) {
       for (int q = 0; q < r; ++q) ex += vload(V, v64, i * ldv + q) * psi[q] * vload(V, v64, int64_t(j) * ldv + q);
     }
+    // self-check of the screen: |screened - |exact|| must stay within the bound
+    const double serr = j >= 0 ? fabs(double(cval[mi * kC + lane]) - fabs(ex)) : 0.0;
     double key = j >= 0 ? fabs(ex) : -1.0;
     int kj = j >= 0 ? j : INT_MAX;
     double sv = ex;
@@ -208,6 +212,11 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
     bnd = warp_sum(bnd);
     nrm = sqrt(warp_sum(nrm)) * (1.0 + 1e-12);
     bnd = fmin(bnd, nrm * double(__uint_as_float(colmax_bits[r]))) * u;
+    {
+      double ratio = bnd > 0.0 ? serr / bnd : (serr > 0.0 ? 1e30 : 0.0);
+      ratio = warp_max(ratio);
+      if (lane == 0 && ratio > 0.0) atomicMax(err_bits, __float_as_uint(float(fmin(ratio, 1e30))));
+    }
     const double qk = __shfl_sync(0xffffffffu, key, k - 1);
     const double t = double(thr[mi]);
     const bool certified = t < 0.0 || qk > t + bnd;
@@ -304,13 +313,13 @@ double screen_unit(gmgm_prec prec, int r) {
 }
 
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
-                    const int* rows, const int* count_dev, const int32_t* cidx, const float* /*cval*/,
+                    const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
                     const float* thr, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
-                    int* flag_list, int* flag_count) {
-  const int64_t m = rows ? d : d;  // grid covers d rows at most
-  const unsigned blocks = unsigned(std::min<int64_t>((m * 32 + 255) / 256, 65536));
-  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, thr, colmax_bits, u,
-                                        idx, val, flag_list, flag_count);
+                    int* flag_list, int* flag_count, unsigned* err_bits) {
+  // one warp per row; the grid covers at most d rows (grid-stride beyond)
+  const unsigned blocks = unsigned(std::min<int64_t>((d * 32 + 255) / 256, 65536));
+  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, cval, thr, colmax_bits,
+                                        u, idx, val, flag_list, flag_count, err_bits);
 }
 
 void launch_exact_rows(cudaStream_t s, int num_sms, int64_t d, int r, const void* V, int v64, int64_t ldv,
@@ -377,14 +386,15 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   }
   if (st) cudaEventRecord(ev[1], s);
   launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, colmax, screen_unit(prec, r),
-                 idx, val, flag1, counters + 0);
+                 idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
   const int* lvl3 = flag1;
   const int* lvl3_count = counters + 0;
   if (prec != GMGM_FP32) {
     screen_fp32_kernel<<<unsigned(h->num_sms) * 2, 256, smem, s>>>(A, B, d, rpad, flag1, 0, counters + 0, cidx2,
                                                                    cval2, thr2);
     launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, flag1, counters + 0, cidx2, cval2, thr2, colmax,
-                   screen_unit(GMGM_FP32, r), idx, val, flag2, counters + 1);
+                   screen_unit(GMGM_FP32, r), idx, val, flag2, counters + 1,
+                   reinterpret_cast<unsigned*>(counters + 3));
     lvl3 = flag2;
     lvl3_count = counters + 1;
   }
@@ -393,16 +403,21 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   if (st) cudaEventRecord(ev[2], s);
   GMGM_CUDA_TRY(h, cudaGetLastError());
   if (st) {
-    int hc[2] = {0, 0};
-    GMGM_CUDA_TRY(h, cudaMemcpyAsync(hc, counters, 8, cudaMemcpyDeviceToHost, s));
+    unsigned hc[4] = {0, 0, 0, 0};
+    GMGM_CUDA_TRY(h, cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, s));
     GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
     float t1 = 0.f, t2 = 0.f;
     cudaEventElapsedTime(&t1, ev[0], ev[1]);
     cudaEventElapsedTime(&t2, ev[1], ev[2]);
-    st->rows_uncertified = hc[0];
+    float e1, e2;
+    memcpy(&e1, &hc[2], 4);
+    memcpy(&e2, &hc[3], 4);
+    st->rows_uncertified = int64_t(hc[0]);
+    st->rows_exact = int64_t(prec == GMGM_FP32 ? hc[0] : hc[1]);
     st->candidates = kC;
     st->screen_ms = t1;
     st->rescore_ms = t2;
+    st->screen_err_ratio = std::max(double(e1), double(e2));
     for (auto& e : ev) cudaEventDestroy(e);
   }
   return GMGM_OK;

@@ -1,16 +1,324 @@
-// Tensor-core (tcgen05) screen for the top-k network path.
+// Tensor-core screen for the per-row top-k of Psi = V diag(psi) V^T
+// (Algorithm 1: threshold simultaneously with recomposition), sm_103a.
+//
+// Persistent, warp-specialised kernel, one CTA per SM:
+//   warp 0      TMA producer: the CTA's A rows (bf16(V psi), 256 rows = two
+//               128-row MMA tiles) once per row block, then every B tile
+//               (bf16(V), 128 rows) into a 6-stage shared-memory ring;
+//   warp 1      MMA issuer (one thread): per B tile, two accumulators
+//               D_h[128 x 128] = A_h B^T (K = 64 in four K=16 steps), FP32 in
+//               TMEM, double-buffered (4 x 128 of the 512 TMEM columns);
+//   warps 2-9   epilogue: thread = one row; tcgen05.ld 32 columns at a time,
+//               the chunk's max |v| against the row's running kC-th best
+//               (one FMNMX per element), and only when it beats it an insert
+//               into the row's kC-slot candidate list (shared memory).
+// All CTAs sweep the B tiles in the same order, so a B tile read from HBM
+// by the first CTA is served from L2 to the others.  Every wait is bounded;
+// on timeout the kernel records GMGM_DEV_TIMEOUT and leaves after freeing
+// its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
+#include "device.cuh"
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 #include "topk_common.cuh"
 
 namespace gmgm {
+namespace {
 
-size_t topk_tc_scratch_bytes(int64_t, int, gmgm_prec) { return 0; }
+constexpr int kTM = 128;                    // rows per MMA tile
+constexpr int kHalves = 2;                  // MMA tiles per row block
+constexpr int kRB = kTM * kHalves;          // rows per row block
+constexpr int kTN = 128;                    // columns per B tile
+constexpr int kKP = 64;                     // padded K (bf16 elements, one 128-byte row)
+constexpr int kStages = 6;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kTileBytes = kTM * kKP * 2;   // 16 KB, A tile and B tile alike
+constexpr long long kSpin = 1ll << 23;      // polls per bounded wait
 
-cudaError_t launch_screen_tc(gmgm_handle*, int64_t, int, const void*, int, int64_t, const double*, gmgm_prec,
-                             int32_t*, float*, float*, void*) {
-  return cudaErrorNotSupported;
+struct __align__(8) Bars {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t accf[2];
+  uint64_t acce[2];
+  uint64_t afull;
+  uint64_t aempty;
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+constexpr size_t kSmemBytes = 1024 /*align slack*/ + size_t(kHalves) * kTileBytes + size_t(kStages) * kTileBytes +
+                              size_t(2) * kC * kRB * 4 + sizeof(Bars);
+
+__device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
+  atomicExch(&bs->abort, 1);
+  set_status(status, GMGM_DEV_TIMEOUT);
+}
+
+__device__ __forceinline__ bool aborted(Bars* bs) { return *reinterpret_cast<volatile int*>(&bs->abort) != 0; }
+
+// Candidate list of one row, slot-major (stride kRB) so a warp's rows are
+// consecutive words.  Same policy as list_offer: fill, then replace the
+// minimum only by a strictly larger value.  Kept out of line (inserts are
+// rare); the state travels by value so it stays in registers.
+struct ListState {
+  int cnt;
+  int minpos;
+  float minv;
+};
+
+__device__ __noinline__ ListState offer_strided(float* lv, int* li, ListState st, float v, int j) {
+  if (st.cnt < kC) {
+    lv[st.cnt * kRB] = v;
+    li[st.cnt * kRB] = j;
+    ++st.cnt;
+    if (st.cnt < kC) return st;
+  } else {
+    lv[st.minpos * kRB] = v;
+    li[st.minpos * kRB] = j;
+  }
+  st.minv = lv[0];
+  st.minpos = 0;
+  for (int c = 1; c < kC; ++c)
+    if (lv[c * kRB] < st.minv) st.minv = lv[c * kRB], st.minpos = c;
+  return st;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    screen_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n,
+                     int ksteps, int32_t* __restrict__ cand_idx, float* __restrict__ cand_val,
+                     float* __restrict__ thr_out, int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + kHalves * kTileBytes;
+  float* lv = reinterpret_cast<float*>(sB + kStages * kTileBytes);
+  int* li = reinterpret_cast<int*>(lv + kC * kRB);
+  Bars* bs = reinterpret_cast<Bars*>(li + kC * kRB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
+    for (int b = 0; b < 2; ++b) tc::mbar_init(&bs->accf[b], 1), tc::mbar_init(&bs->acce[b], kEpiWarps);
+    tc::mbar_init(&bs->afull, 1);
+    tc::mbar_init(&bs->aempty, 1);
+    tc::mbar_init(&bs->done, 1);
+    bs->abort = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) tc::tmem_alloc(&bs->tmem_base, 512);
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = bs->tmem_base;
+  const int nrb = (n + kRB - 1) / kRB;
+  const int ntiles = (n + kTN - 1) / kTN;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      long long issued = 0;
+      int rbi = 0;
+      for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x, ++rbi) {
+        if (!tc::mbar_wait(&bs->aempty, (rbi & 1) ^ 1, kSpin)) {
+          raise_abort(bs, status);
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&bs->afull, kHalves * kTileBytes);
+        for (int hh = 0; hh < kHalves; ++hh) tc::tma_load_2d(sA + hh * kTileBytes, &tmA, &bs->afull, 0, rb * kRB + hh * kTM);
+        for (int t = 0; t < ntiles; ++t, ++issued) {
+          const int s = int(issued % kStages);
+          const uint32_t k = uint32_t(issued / kStages);
+          if (!tc::mbar_wait(&bs->empty[s], (k & 1) ^ 1, kSpin)) {
+            raise_abort(bs, status);
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&bs->full[s], kTileBytes);
+          tc::tma_load_2d(sB + s * kTileBytes, &tmB, &bs->full[s], 0, t * kTN);
+        }
+        if (aborted(bs)) break;
+      }
+      if (aborted(bs)) {
+        // let the loads already in flight land before the CTA can exit
+        for (long long x = issued > kStages ? issued - kStages : 0; x < issued; ++x)
+          tc::mbar_wait(&bs->full[x % kStages], uint32_t(x / kStages) & 1, kSpin);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
+      long long used = 0, accu = 0;
+      int rbi = 0;
+      for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x, ++rbi) {
+        if (!tc::mbar_wait(&bs->afull, rbi & 1, kSpin)) {
+          raise_abort(bs, status);
+          break;
+        }
+        for (int t = 0; t < ntiles; ++t, ++used, ++accu) {
+          const int s = int(used % kStages);
+          const int b = int(accu & 1);
+          if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kStages) & 1, kSpin) ||
+              !tc::mbar_wait(&bs->acce[b], (uint32_t(accu >> 1) & 1) ^ 1, kSpin)) {
+            raise_abort(bs, status);
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t bbase = tc::smem_u32(sB + s * kTileBytes);
+#pragma unroll
+          for (int hh = 0; hh < kHalves; ++hh) {
+            const uint32_t abase = tc::smem_u32(sA + hh * kTileBytes);
+            const uint32_t d = tmem + uint32_t((b * kHalves + hh) * kTN);
+            for (int ks = 0; ks < ksteps; ++ks)
+              tc::mma_bf16(d, tc::sdesc_k128(abase + ks * 32), tc::sdesc_k128(bbase + ks * 32), idesc, ks > 0);
+          }
+          tc::mma_commit(&bs->empty[s]);
+          tc::mma_commit(&bs->accf[b]);
+        }
+        tc::mma_commit(&bs->aempty);
+      }
+      // drain: every MMA issued so far has completed once `done` fires
+      tc::mma_commit(&bs->done);
+      tc::mbar_wait(&bs->done, 0, kSpin);
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int ew = warp - 2;
+    const int half = ew >> 2;
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row_local = half * kTM + q * 32 + lane;
+    float* mlv = lv + row_local;
+    int* mli = li + row_local;
+    long long accu = 0;
+    for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x) {
+      const int i = rb * kRB + row_local;
+      ListState st{0, 0, -1.f};
+      for (int t = 0; t < ntiles; ++t, ++accu) {
+        const int b = int(accu & 1);
+        if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin)) {
+          raise_abort(bs, status);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t((b * kHalves + half) * kTN);
+        const int j0 = t * kTN;
+#pragma unroll 1
+        for (int c = 0; c < kTN / 32; ++c) {
+          uint32_t r[32];
+          __syncwarp();
+          tc::tmem_ld_32x32b_x32(taddr + c * 32, r);
+          tc::tmem_ld_wait();
+          float m = 0.f;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) m = fmaxf(m, fabsf(__uint_as_float(r[e])));
+          if (m > st.minv) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const float v = fabsf(__uint_as_float(r[e]));
+              const int j = j0 + c * 32 + e;
+              if (v > st.minv && j < n && j != i) st = offer_strided(mlv, mli, st, v, j);
+            }
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
+      }
+      if (i < n && !aborted(bs)) {
+        for (int c = 0; c < kC; ++c) {
+          cand_idx[int64_t(i) * kC + c] = c < st.cnt ? mli[c * kRB] : -1;
+          cand_val[int64_t(i) * kC + c] = c < st.cnt ? mlv[c * kRB] : -1.f;
+        }
+        thr_out[i] = st.cnt >= kC ? st.minv : -1.f;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// bf16 operands of the screen: A = bf16(V psi), B = bf16(V), n x 64, K zero-padded.
+__global__ void prep_tc_kernel(const void* V, int v64, int64_t ldv, const double* __restrict__ psi, int64_t n, int r,
+                               __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B) {
+  const int64_t total = n * kKP;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / kKP;
+    const int k = int(e - i * kKP);
+    double v = 0.0;
+    if (k < r) v = v64 ? static_cast<const double*>(V)[i * ldv + k] : double(static_cast<const float*>(V)[i * ldv + k]);
+    A[e] = __float2bfloat16_rn(k < r ? float(v * psi[k]) : 0.f);
+    B[e] = __float2bfloat16_rn(float(v));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// rows x 64 bf16, row-major; box 128 rows x 64 (one 128-byte swizzle span)
+bool make_map(CUtensorMap* m, void* base, int64_t rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cuuint64_t(kKP), cuuint64_t(rows)};
+  cuuint64_t strides[1] = {cuuint64_t(kKP) * 2};
+  cuuint32_t box[2] = {cuuint32_t(kKP), cuuint32_t(kTM)};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t topk_tc_scratch_bytes(int64_t d, int r, gmgm_prec prec) {
+  if (prec != GMGM_BF16) return 0;
+  return Carve::round(size_t(d) * kKP * 2) * 2 + 1024;
+}
+
+cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi,
+                             gmgm_prec prec, int32_t* cidx, float* cval, float* thr, void* scratch) {
+  if (prec != GMGM_BF16 || r > kKP || d > (int64_t(1) << 30)) return cudaErrorNotSupported;
+  Carve c(scratch);
+  __nv_bfloat16* A = c.take<__nv_bfloat16>(size_t(d) * kKP);
+  __nv_bfloat16* B = c.take<__nv_bfloat16>(size_t(d) * kKP);
+  {
+    const int64_t total = d * kKP;
+    const unsigned blocks = unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 16));
+    prep_tc_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, A, B);
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, d) || !make_map(&mb, B, d)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
+  if (e != cudaSuccess) return e;
+  const int nrb = int((d + kRB - 1) / kRB);
+  const int grid = std::min(nrb, h->num_sms);
+  const int ksteps = (r + 15) / 16;
+  screen_tc_kernel<<<grid, kThreads, kSmemBytes, h->stream>>>(ma, mb, int(d), ksteps, cidx, cval, thr, h->d_status);
+  note_launch(2);
+  return cudaGetLastError();
 }
 
 }  // namespace gmgm

@@ -47,7 +47,7 @@ double screen_unit(gmgm_prec prec, int r);
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
                     const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
                     const float* thr, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
-                    int* flag_list, int* flag_count);
+                    int* flag_list, int* flag_count, unsigned* err_bits);
 
 // exact FP64 scan of the listed rows (device-side count)
 void launch_exact_rows(cudaStream_t s, int num_sms, int64_t d, int r, const void* V, int v64, int64_t ldv,

@@ -222,6 +222,24 @@ def test_topk_fp32_random(g, cuda_dev, d, r, k):
     idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(lam).to(cuda_dev), k)
     frac = _check_topk(V.astype(np.float64), lam, k, idx.cpu().numpy(), val.cpu().numpy())
     assert frac > 0.9
+    assert st["screen_err_ratio"] <= 1.0, st
+
+
+@pytest.mark.parametrize("d,r,k", [(3000, 50, 10), (1000, 64, 20), (257, 7, 5), (100, 16, 32), (40, 3, 5)])
+def test_topk_bf16_tensor_core_screen(g, cuda_dev, d, r, k):
+    # tcgen05 screen + FP64 rescoring: exact FP64 top-k where the gap allows,
+    # the screen inside its stated error bound, and most rows certified by
+    # the tensor-core screen itself (a broken screen would flag every row).
+    rng = _rng(100 + d)
+    V = rng.standard_normal((d, r)).astype(np.float32)
+    lam = rng.uniform(0.1, 2.0, r)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(lam).to(cuda_dev), k,
+                                  prec=g.BF16)
+    frac = _check_topk(V.astype(np.float64), lam, k, idx.cpu().numpy(), val.cpu().numpy())
+    assert frac > 0.9
+    assert st["screen_err_ratio"] <= 1.0, st
+    if d > 64 and k <= 20:  # with k near the 32 candidate slots no row can be certified
+        assert st["rows_uncertified"] <= 0.5 * d, st
 
 
 def test_topk_fp64_input_and_ties(g, cuda_dev):
