@@ -263,6 +263,28 @@ def main():
         return g.fit_two_axis(x, a.r_cells, a.genes, a.k_cells, a.k_genes, gram_prec=gram_prec,
                               topk_prec=topk_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, tol=a.tol, h=h)
 
+    def staged_step(src):
+        """The same step, stage by stage, with events between stages (untimed)."""
+        names = ["preprocess", "gram", "eig", "lift", "solve", "topk_cells", "topk_genes"]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(stream)
+        x, hi, lo, ld_t = g.preprocess(src, split=split, h=h)
+        ev[1].record(stream)
+        S = g.gram(x, g.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
+        ev[2].record(stream)
+        e_all, W = g.spectra(S, a.genes, True, h=h)
+        ev[3].record(stream)
+        U = g.lift(x, W[:, :a.r_cells].contiguous(), e_all[:a.r_cells].contiguous(), a.r_cells, h=h)
+        ev[4].record(stream)
+        (lr, lc), _ = g.eigsolve([e_all[:a.r_cells].contiguous(), e_all], [(0, 1)], tol=a.tol, h=h)
+        ev[5].record(stream)
+        g.topk_network(U, lr, a.k_cells, topk_prec, h=h)
+        ev[6].record(stream)
+        g.topk_network(W, lc, a.k_genes, g.FP32, h=h)
+        ev[7].record(stream)
+        torch.cuda.synchronize()
+        return {n: round(ev[i].elapsed_time(ev[i + 1]), 3) for i, n in enumerate(names)}
+
     def barrier():
         if world > 1:
             dist.barrier()
@@ -270,6 +292,8 @@ def main():
 
     for _ in range(a.warmup):
         res = step(counts)
+    barrier()
+    stage_ms = staged_step(counts)
     barrier()
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
@@ -374,7 +398,7 @@ def main():
                    "l2": "inputs larger than L2 (8 GB counts per step)", "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clocks,
-        "detail": {"solve": solve, "rows_uncertified": unc, "screen_ms": scr_ms,
+        "detail": {"stage_ms": stage_ms, "solve": solve, "rows_uncertified": unc, "screen_ms": scr_ms,
                    "gene_topk": res.topk_cols_stats},
     }
     print(json.dumps(line), flush=True)

@@ -210,27 +210,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_after_sync();
         const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t((b * kHalves + half) * kTN);
         const int j0 = t * kTN;
-#pragma unroll 1
-        for (int c = 0; c < kTN / 32; ++c) {
-          uint32_t r[32];
-          __syncwarp();
-          tc::tmem_ld_32x32b_x32(taddr + c * 32, r);
-          tc::tmem_ld_wait();
-          float m = 0.f;
+        // the whole 128-column row slice in one round trip, then hand the
+        // accumulator back to the MMA warp before scanning
+        uint32_t r[kTN / 32][32];
+        __syncwarp();
 #pragma unroll
-          for (int e = 0; e < 32; ++e) m = fmaxf(m, fabsf(__uint_as_float(r[e])));
-          if (m > st.minv) {
+        for (int c = 0; c < kTN / 32; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
+        tc::tmem_ld_wait();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
+#pragma unroll
+        for (int c = 0; c < kTN / 32; ++c) {
+          float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // four short max chains
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            m0 = fmaxf(m0, fabsf(__uint_as_float(r[c][e + 0])));
+            m1 = fmaxf(m1, fabsf(__uint_as_float(r[c][e + 1])));
+            m2 = fmaxf(m2, fabsf(__uint_as_float(r[c][e + 2])));
+            m3 = fmaxf(m3, fabsf(__uint_as_float(r[c][e + 3])));
+          }
+          if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > st.minv) {
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
-              const float v = fabsf(__uint_as_float(r[e]));
+              const float v = fabsf(__uint_as_float(r[c][e]));
               const int j = j0 + c * 32 + e;
               if (v > st.minv && j < n && j != i) st = offer_strided(mlv, mli, st, v, j);
             }
           }
         }
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
       }
       if (i < n && !aborted(bs)) {
         for (int c = 0; c < kC; ++c) {
