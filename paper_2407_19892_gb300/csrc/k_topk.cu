@@ -9,9 +9,8 @@
 //            psi, sorts (|value| desc, column asc) and certifies the row: the
 //            k-th exact value must exceed the best excluded screened value
 //            plus a rigorous bound on the screen's error;
-//   repair   rows that fail a tensor-core screen are screened again in FP32
-//            (rows gathered) and rescored; rows that still fail are scanned
-//            exactly in FP64.
+//   repair   rows that fail are scanned exactly in FP64, column-parallel
+//            (a row's columns split over many CTAs, then merged).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -233,35 +232,37 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
 
 constexpr int kExThreads = 256;
 
-// Exact FP64 scan of the listed rows, one CTA per row: per-thread sorted
-// top-k lists, then k rounds of a block-wide arg-best over the list heads.
-__global__ void __launch_bounds__(kExThreads) exact_rows_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv,
-                                                                 const double* __restrict__ psi, int k,
-                                                                 const int* __restrict__ rows,
-                                                                 const int* __restrict__ count_dev,
-                                                                 int32_t* __restrict__ idx_out,
-                                                                 float* __restrict__ val_out) {
+// Exact FP64 top-k of one (listed row, column chunk) work item per CTA:
+// per-thread sorted lists, then k rounds of a block-wide arg-best over the
+// list heads.  Writes the chunk's k best (value, column) to part[w][k].
+__global__ void __launch_bounds__(kExThreads) exact_chunk_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv,
+                                                                  const double* __restrict__ psi, int k,
+                                                                  const int* __restrict__ rows, int row0, int nb,
+                                                                  int nchunks, int64_t chunk,
+                                                                  double* __restrict__ part_v,
+                                                                  int* __restrict__ part_j) {
   extern __shared__ double esm[];
-  double* a = esm;                                       // [r]
-  double* lvv = a + r;                                   // [threads][k] signed values
+  double* a = esm;                                         // [r]
+  double* lvv = a + r;                                     // [threads][k]
   int* lj = reinterpret_cast<int*>(lvv + kExThreads * k);  // [threads][k]
   __shared__ double bkey[kExThreads];
   __shared__ int bj[kExThreads];
   __shared__ int bt[kExThreads];
-  const int m = *count_dev;
-  for (int mi = blockIdx.x; mi < m; mi += gridDim.x) {
-    const int64_t i = rows[mi];
+  const int64_t items = int64_t(nb) * nchunks;
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const int rl = int(w / nchunks), ch = int(w - int64_t(rl) * nchunks);
+    const int64_t i = rows[row0 + rl];
     for (int q = threadIdx.x; q < r; q += blockDim.x) a[q] = vload(V, v64, i * ldv + q) * psi[q];
     __syncthreads();
     double* mv = lvv + threadIdx.x * k;
     int* mj = lj + threadIdx.x * k;
     int cnt = 0;
-    for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+    const int64_t jb = int64_t(ch) * chunk, je = jb + chunk < d ? jb + chunk : d;
+    for (int64_t j = jb + threadIdx.x; j < je; j += blockDim.x) {
       if (j == i) continue;
       double ex = 0.0;
       for (int q = 0; q < r; ++q) ex += a[q] * vload(V, v64, j * ldv + q);
       const double ax = fabs(ex);
-      // sorted insertion (best first)
       int pos = cnt < k ? cnt : k;
       while (pos > 0 && better(ax, int(j), fabs(mv[pos - 1]), mj[pos - 1])) --pos;
       if (pos < k) {
@@ -286,16 +287,67 @@ __global__ void __launch_bounds__(kExThreads) exact_rows_kernel(int64_t d, int r
         }
         __syncthreads();
       }
-      const int win = bt[0];
-      if (threadIdx.x == win) {
-        idx_out[i * k + out] = head < cnt ? mj[head] : -1;
-        val_out[i * k + out] = head < cnt ? float(mv[head]) : 0.f;
+      if (threadIdx.x == bt[0]) {
+        part_v[w * k + out] = head < cnt ? mv[head] : 0.0;
+        part_j[w * k + out] = head < cnt ? mj[head] : -1;
         ++head;
       }
       __syncthreads();
     }
   }
 }
+
+// Merge the per-chunk lists of one listed row into its exact top-k.
+__global__ void __launch_bounds__(kExThreads) exact_merge_kernel(const int* __restrict__ rows, int row0, int nchunks,
+                                                                  int k, const double* __restrict__ part_v,
+                                                                  const int* __restrict__ part_j,
+                                                                  int32_t* __restrict__ idx_out,
+                                                                  float* __restrict__ val_out) {
+  extern __shared__ double msm[];
+  const int rl = blockIdx.x;
+  const int64_t i = rows[row0 + rl];
+  const int m = nchunks * k;
+  double* key = msm;                                // [m] |value|, -2 once taken
+  int* col = reinterpret_cast<int*>(key + m);      // [m]
+  __shared__ double bkey[kExThreads];
+  __shared__ int bj[kExThreads];
+  __shared__ int bp[kExThreads];
+  const double* pv = part_v + int64_t(rl) * m;
+  const int* pj = part_j + int64_t(rl) * m;
+  for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    key[e] = pj[e] >= 0 ? fabs(pv[e]) : -1.0;
+    col[e] = pj[e] >= 0 ? pj[e] : INT_MAX;
+  }
+  __syncthreads();
+  for (int out = 0; out < k; ++out) {
+    double bk = -3.0;
+    int bc = INT_MAX, bpos = -1;
+    for (int e = threadIdx.x; e < m; e += blockDim.x)
+      if (better(key[e], col[e], bk, bc)) bk = key[e], bc = col[e], bpos = e;
+    bkey[threadIdx.x] = bk;
+    bj[threadIdx.x] = bc;
+    bp[threadIdx.x] = bpos;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        const int o = threadIdx.x + s;
+        if (better(bkey[o], bj[o], bkey[threadIdx.x], bj[threadIdx.x]))
+          bkey[threadIdx.x] = bkey[o], bj[threadIdx.x] = bj[o], bp[threadIdx.x] = bp[o];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const int e = bp[0];
+      const bool ok = e >= 0 && pj[e] >= 0;
+      idx_out[i * k + out] = ok ? pj[e] : -1;
+      val_out[i * k + out] = ok ? float(pv[e]) : 0.f;
+      if (e >= 0) key[e] = -2.0;
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int64_t kExactCap = int64_t(1) << 22;  // partial entries held at once
 
 }  // namespace
 
@@ -322,12 +374,30 @@ void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, in
                                         u, idx, val, flag_list, flag_count, err_bits);
 }
 
-void launch_exact_rows(cudaStream_t s, int num_sms, int64_t d, int r, const void* V, int v64, int64_t ldv,
-                       const double* psi, int k, const int* rows, const int* count_dev, int32_t* idx, float* val) {
+// Exact FP64 top-k of the listed rows, column-parallel: a row's columns are
+// split into chunks (one CTA each), then merged.  Batched so the partial
+// lists stay within kExactCap entries.
+int run_exact_rows(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
+                   const int* rows, int nrows, double* part_v, int* part_j, int32_t* idx, float* val) {
+  if (nrows <= 0) return GMGM_OK;
+  const int64_t chunk = std::max<int64_t>(8192, (d + 255) / 256);
+  const int nchunks = int((d + chunk - 1) / chunk);
+  const int per_batch = int(std::max<int64_t>(1, std::min<int64_t>(nrows, kExactCap / (int64_t(nchunks) * k))));
   const size_t smem = size_t(r) * 8 + size_t(kExThreads) * k * 12;
-  cudaFuncSetAttribute(exact_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  exact_rows_kernel<<<unsigned(num_sms) * 2, kExThreads, smem, s>>>(d, r, V, v64, ldv, psi, k, rows, count_dev, idx,
-                                                                   val);
+  const size_t msmem = size_t(nchunks) * k * 12;
+  GMGM_CUDA_TRY(h, cudaFuncSetAttribute(exact_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  GMGM_CUDA_TRY(h, cudaFuncSetAttribute(exact_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(msmem)));
+  for (int row0 = 0; row0 < nrows; row0 += per_batch) {
+    const int nb = std::min(per_batch, nrows - row0);
+    const unsigned grid = unsigned(std::min<int64_t>(int64_t(nb) * nchunks, int64_t(h->num_sms) * 8));
+    exact_chunk_kernel<<<grid, kExThreads, smem, h->stream>>>(d, r, V, v64, ldv, psi, k, rows, row0, nb, nchunks,
+                                                             chunk, part_v, part_j);
+    exact_merge_kernel<<<unsigned(nb), kExThreads, msmem, h->stream>>>(rows, row0, nchunks, k, part_v, part_j, idx,
+                                                                      val);
+    note_launch(2);
+  }
+  GMGM_CUDA_TRY(h, cudaGetLastError());
+  return GMGM_OK;
 }
 
 size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
@@ -337,9 +407,8 @@ size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
   b += Carve::round(size_t(r + 1) * 4);         // colmax + max row norm
   b += Carve::round(size_t(d) * kC * 4) * 2;    // level-1 candidates
   b += Carve::round(size_t(d) * 4);             // level-1 thr
-  b += Carve::round(size_t(d) * 4) * 2;         // flag lists
-  b += Carve::round(size_t(d) * kC * 4) * 2;    // level-2 candidates
-  b += Carve::round(size_t(d) * 4);             // level-2 thr
+  b += Carve::round(size_t(d) * 4);             // flag list
+  b += Carve::round(size_t(kExactCap) * 12) + 256;  // exact partial lists
   b += Carve::round(64);                        // counters
   b += Carve::round(topk_tc_scratch_bytes(d, r, prec));
   return b + 4096;
@@ -357,10 +426,8 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   float* cval = c.take<float>(size_t(d) * kC);
   float* thr = c.take<float>(d);
   int* flag1 = c.take<int>(d);
-  int* flag2 = c.take<int>(d);
-  int32_t* cidx2 = c.take<int32_t>(size_t(d) * kC);
-  float* cval2 = c.take<float>(size_t(d) * kC);
-  float* thr2 = c.take<float>(d);
+  double* part_v = c.take<double>(kExactCap);
+  int* part_j = c.take<int>(kExactCap);
   int* counters = c.take<int>(16);
   void* tc_scratch = c.take<char>(topk_tc_scratch_bytes(d, r, prec));
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -387,19 +454,14 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   if (st) cudaEventRecord(ev[1], s);
   launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, colmax, screen_unit(prec, r),
                  idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
-  const int* lvl3 = flag1;
-  const int* lvl3_count = counters + 0;
-  if (prec != GMGM_FP32) {
-    screen_fp32_kernel<<<unsigned(h->num_sms) * 2, 256, smem, s>>>(A, B, d, rpad, flag1, 0, counters + 0, cidx2,
-                                                                   cval2, thr2);
-    launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, flag1, counters + 0, cidx2, cval2, thr2, colmax,
-                   screen_unit(GMGM_FP32, r), idx, val, flag2, counters + 1,
-                   reinterpret_cast<unsigned*>(counters + 3));
-    lvl3 = flag2;
-    lvl3_count = counters + 1;
-  }
-  launch_exact_rows(s, h->num_sms, d, r, V, v_fp64, ldv, psi, k, lvl3, lvl3_count, idx, val);
-  note_launch(prec == GMGM_FP32 ? 5 : 6);
+  note_launch(prec == GMGM_FP32 ? 4 : 3);
+  // rows the screen could not certify: exact FP64 scan (the count is read
+  // back once to size the work)
+  int nflag = 0;
+  GMGM_CUDA_TRY(h, cudaMemcpyAsync(&nflag, counters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
+  int rc = run_exact_rows(h, d, r, V, v_fp64, ldv, psi, k, flag1, nflag, part_v, part_j, idx, val);
+  if (rc) return rc;
   if (st) cudaEventRecord(ev[2], s);
   GMGM_CUDA_TRY(h, cudaGetLastError());
   if (st) {
@@ -409,15 +471,14 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     float t1 = 0.f, t2 = 0.f;
     cudaEventElapsedTime(&t1, ev[0], ev[1]);
     cudaEventElapsedTime(&t2, ev[1], ev[2]);
-    float e1, e2;
+    float e1;
     memcpy(&e1, &hc[2], 4);
-    memcpy(&e2, &hc[3], 4);
     st->rows_uncertified = int64_t(hc[0]);
-    st->rows_exact = int64_t(prec == GMGM_FP32 ? hc[0] : hc[1]);
+    st->rows_exact = int64_t(nflag);
     st->candidates = kC;
     st->screen_ms = t1;
     st->rescore_ms = t2;
-    st->screen_err_ratio = std::max(double(e1), double(e2));
+    st->screen_err_ratio = double(e1);
     for (auto& e : ev) cudaEventDestroy(e);
   }
   return GMGM_OK;

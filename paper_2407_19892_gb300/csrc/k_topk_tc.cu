@@ -35,7 +35,8 @@ constexpr int kHalves = 2;                  // MMA tiles per row block
 constexpr int kRB = kTM * kHalves;          // rows per row block
 constexpr int kTN = 128;                    // columns per B tile
 constexpr int kKP = 64;                     // padded K (bf16 elements, one 128-byte row)
-constexpr int kStages = 6;
+constexpr int kStages = 5;
+constexpr int kStage = 33;                  // staging row stride (floats) for inserts
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileBytes = kTM * kKP * 2;   // 16 KB, A tile and B tile alike
@@ -54,7 +55,7 @@ struct __align__(8) Bars {
 };
 
 constexpr size_t kSmemBytes = 1024 /*align slack*/ + size_t(kHalves) * kTileBytes + size_t(kStages) * kTileBytes +
-                              size_t(2) * kC * kRB * 4 + sizeof(Bars);
+                              size_t(2) * kC * kRB * 4 + size_t(kEpiWarps) * 32 * kStage * 4 + sizeof(Bars);
 
 __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
   atomicExch(&bs->abort, 1);
@@ -100,7 +101,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sB = sA + kHalves * kTileBytes;
   float* lv = reinterpret_cast<float*>(sB + kStages * kTileBytes);
   int* li = reinterpret_cast<int*>(lv + kC * kRB);
-  Bars* bs = reinterpret_cast<Bars*>(li + kC * kRB);
+  float* stage = reinterpret_cast<float*>(li + kC * kRB);  // [kEpiWarps][32][kStage]
+  Bars* bs = reinterpret_cast<Bars*>(stage + kEpiWarps * 32 * kStage);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue ----------------
     const int ew = warp - 2;
+    float* mstage = stage + (ew * 32 + lane) * kStage;
     const int half = ew >> 2;
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int row_local = half * kTM + q * 32 + lane;
@@ -230,13 +233,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             m2 = fmaxf(m2, fabsf(__uint_as_float(r[c][e + 2])));
             m3 = fmaxf(m3, fabsf(__uint_as_float(r[c][e + 3])));
           }
-          if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > st.minv) {
+          const bool hit = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > st.minv;
+          if (__any_sync(0xffffffffu, hit)) {
+            // rare: stage the chunk in shared memory and insert with a rolled
+            // loop (keeps the hot loop small for the instruction cache)
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float v = fabsf(__uint_as_float(r[c][e]));
-              const int j = j0 + c * 32 + e;
-              if (v > st.minv && j < n && j != i) st = offer_strided(mlv, mli, st, v, j);
+            for (int e = 0; e < 32; ++e) mstage[e] = __uint_as_float(r[c][e]);
+            __syncwarp();
+            if (hit) {
+#pragma unroll 1
+              for (int e = 0; e < 32; ++e) {
+                const float v = fabsf(mstage[e]);
+                const int j = j0 + c * 32 + e;
+                if (v > st.minv && j < n && j != i) st = offer_strided(mlv, mli, st, v, j);
+              }
             }
+            __syncwarp();
           }
         }
       }

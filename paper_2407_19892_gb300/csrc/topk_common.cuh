@@ -49,10 +49,6 @@ void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, in
                     const float* thr, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
                     int* flag_list, int* flag_count, unsigned* err_bits);
 
-// exact FP64 scan of the listed rows (device-side count)
-void launch_exact_rows(cudaStream_t s, int num_sms, int64_t d, int r, const void* V, int v64, int64_t ldv,
-                       const double* psi, int k, const int* rows, const int* count_dev, int32_t* idx, float* val);
-
 // tensor-core screen (BF16 / 3xBF16) over all rows
 size_t topk_tc_scratch_bytes(int64_t d, int r, gmgm_prec prec);
 cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,
