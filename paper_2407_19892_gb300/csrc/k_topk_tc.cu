@@ -35,8 +35,7 @@ constexpr int kHalves = 2;                  // MMA tiles per row block
 constexpr int kRB = kTM * kHalves;          // rows per row block
 constexpr int kTN = 128;                    // columns per B tile
 constexpr int kKP = 64;                     // padded K (bf16 elements, one 128-byte row)
-constexpr int kStages = 5;
-constexpr int kStage = 33;                  // staging row stride (floats) for inserts
+constexpr int kStages = 6;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileBytes = kTM * kKP * 2;   // 16 KB, A tile and B tile alike
@@ -55,7 +54,7 @@ struct __align__(8) Bars {
 };
 
 constexpr size_t kSmemBytes = 1024 /*align slack*/ + size_t(kHalves) * kTileBytes + size_t(kStages) * kTileBytes +
-                              size_t(2) * kC * kRB * 4 + size_t(kEpiWarps) * 32 * kStage * 4 + sizeof(Bars);
+                              size_t(2) * kC * kRB * 4 + sizeof(Bars);
 
 __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
   atomicExch(&bs->abort, 1);
@@ -73,6 +72,21 @@ struct ListState {
   int minpos;
   float minv;
 };
+
+// r[e] for a per-lane runtime e without leaving registers: a 5-level select
+// tree over constant indices (31 selects).
+__device__ __forceinline__ uint32_t pick32(const uint32_t (&r)[32], int e) {
+  uint32_t a[16], b[8], c[4], d[2];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) a[q] = (e & 16) ? r[q + 16] : r[q];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) b[q] = (e & 8) ? a[q + 8] : a[q];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) c[q] = (e & 4) ? b[q + 4] : b[q];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) d[q] = (e & 2) ? c[q + 2] : c[q];
+  return (e & 1) ? d[1] : d[0];
+}
 
 __device__ __noinline__ ListState offer_strided(float* lv, int* li, ListState st, float v, int j) {
   if (st.cnt < kC) {
@@ -101,8 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sB = sA + kHalves * kTileBytes;
   float* lv = reinterpret_cast<float*>(sB + kStages * kTileBytes);
   int* li = reinterpret_cast<int*>(lv + kC * kRB);
-  float* stage = reinterpret_cast<float*>(li + kC * kRB);  // [kEpiWarps][32][kStage]
-  Bars* bs = reinterpret_cast<Bars*>(stage + kEpiWarps * 32 * kStage);
+  Bars* bs = reinterpret_cast<Bars*>(li + kC * kRB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
@@ -194,7 +207,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue ----------------
     const int ew = warp - 2;
-    float* mstage = stage + (ew * 32 + lane) * kStage;
     const int half = ew >> 2;
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int row_local = half * kTM + q * 32 + lane;
@@ -233,22 +245,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             m2 = fmaxf(m2, fabsf(__uint_as_float(r[c][e + 2])));
             m3 = fmaxf(m3, fabsf(__uint_as_float(r[c][e + 3])));
           }
-          const bool hit = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > st.minv;
-          if (__any_sync(0xffffffffu, hit)) {
-            // rare: stage the chunk in shared memory and insert with a rolled
-            // loop (keeps the hot loop small for the instruction cache)
+          if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > st.minv) {
+            // per lane: a bitmask of the columns above the threshold, then
+            // each set bit's value pulled out of registers by a select tree
+            uint32_t mask = 0;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) mstage[e] = __uint_as_float(r[c][e]);
-            __syncwarp();
-            if (hit) {
-#pragma unroll 1
-              for (int e = 0; e < 32; ++e) {
-                const float v = fabsf(mstage[e]);
-                const int j = j0 + c * 32 + e;
-                if (v > st.minv && j < n && j != i) st = offer_strided(mlv, mli, st, v, j);
-              }
+            for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(r[c][e])) > st.minv ? 1u : 0u) << e;
+            while (mask) {
+              const int e = __ffs(mask) - 1;
+              mask &= mask - 1;
+              const float v = fabsf(__uint_as_float(pick32(r[c], e)));
+              const int j = j0 + c * 32 + e;
+              if (v > st.minv && j < n && j != i) st = offer_strided(mlv, mli, st, v, j);
             }
-            __syncwarp();
           }
         }
       }
