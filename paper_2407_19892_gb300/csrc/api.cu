@@ -159,9 +159,7 @@ int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec, do
     if (((uintptr_t)m->xt_hi % 16) || (m->xt_lo && ((uintptr_t)m->xt_lo % 16)))
       return fail(h, GMGM_E_ARG, "gmgm_gram: xt buffers must be 16-byte aligned");
     int splits = gmgm::gram_tc_splits(h, m);
-    size_t tiles = size_t((m->cols + 127) / 128);
-    size_t bytes = size_t(splits) * tiles * tiles * 128 * 128 * sizeof(float);
-    int rc = gmgm::ensure_scratch(h, bytes + 256);
+    int rc = gmgm::ensure_scratch(h, gmgm::gram_tc_scratch_bytes(m));
     if (rc) return rc;
     GMGM_CUDA_TRY(h, gmgm::launch_gram_tc(h, m, prec, S, lds, accumulate,
                                           static_cast<float*>(h->scratch), splits));

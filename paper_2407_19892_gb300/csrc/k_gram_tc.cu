@@ -1,14 +1,311 @@
-// Tensor-core (tcgen05) Gram.
+// Tensor-core Gram S = X^T X (cells x genes X, the small gene axis), sm_103a.
+//
+// Operands are the BF16 planes of X^T written by the preprocessing kernel
+// (gene-major, K = cells contiguous): x = hi + lo.  3xBF16 forms
+// hi.hi^T + hi.lo^T + lo.hi^T (the dropped lo.lo^T is below 2^-16 of each
+// product); plain BF16 forms hi.hi^T only.
+//
+// Work item = (output tile 128 genes x 256 genes of the upper triangle,
+// chunk of kKB 64-cell K blocks).  Persistent CTAs, warp-specialised:
+//   warp 0      TMA producer: per K block the A (128 rows) and B (256 rows)
+//               slices of hi (and lo) into a 2-stage ring;
+//   warp 1      MMA issuer: tcgen05.mma M=128 N=256 K=16, FP32 accumulator
+//               in TMEM (double-buffered, 2 x 256 columns);
+//   warps 2-5   epilogue: tcgen05.ld the accumulator, store the FP32 partial
+//               tile; a second kernel sums the chunks in FP64 and writes both
+//               triangles of S.
+// Every wait is bounded (GMGM_DEV_TIMEOUT on expiry, TMEM freed on exit).
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
+#include "device.cuh"
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace gmgm {
+namespace {
 
-int gram_tc_splits(gmgm_handle*, const gmgm_matrix*) { return 1; }
+constexpr int kGM = 128;                     // tile rows (genes a)
+constexpr int kGN = 256;                     // tile cols (genes b)
+constexpr int kKB = 128;                     // 64-cell K blocks per work item (8192 cells)
+constexpr int kGStages = 2;
+constexpr int kGThreads = 64 + 128;
+constexpr int kABytes = kGM * 128;           // 16 KB per plane
+constexpr int kBBytes = kGN * 128;           // 32 KB per plane
+constexpr int kStageBytes = 2 * (kABytes + kBBytes);
+constexpr long long kGSpin = 1ll << 23;
 
-cudaError_t launch_gram_tc(gmgm_handle*, const gmgm_matrix*, gmgm_prec, double*, int64_t, int, float*, int) {
-  return cudaErrorNotSupported;
+struct __align__(8) GBars {
+  uint64_t full[kGStages];
+  uint64_t empty[kGStages];
+  uint64_t accf[2];
+  uint64_t acce[2];
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+constexpr size_t kGSmem = 1024 + size_t(kGStages) * kStageBytes + sizeof(GBars);
+
+__device__ __forceinline__ bool g_aborted(GBars* bs) { return *reinterpret_cast<volatile int*>(&bs->abort) != 0; }
+__device__ __forceinline__ void g_abort(GBars* bs, int* status) {
+  atomicExch(&bs->abort, 1);
+  set_status(status, GMGM_DEV_TIMEOUT);
+}
+
+// tiles: list of (row tile, col tile) of the upper triangle; nprod: 1 (BF16)
+// or 3 (3xBF16).
+__global__ void __launch_bounds__(kGThreads, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+                   const int2* __restrict__ tiles, int ntiles, int nkb_total, int nchunks, int nprod,
+                   float* __restrict__ part, int* __restrict__ status) {
+  extern __shared__ uint8_t gsm_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
+  GBars* bs = reinterpret_cast<GBars*>(smem + kGStages * kStageBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
+    for (int b = 0; b < 2; ++b) tc::mbar_init(&bs->accf[b], 1), tc::mbar_init(&bs->acce[b], 4);
+    tc::mbar_init(&bs->done, 1);
+    bs->abort = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 1) tc::tmem_alloc(&bs->tmem_base, 512);
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = bs->tmem_base;
+  const int items = ntiles * nchunks;
+  const uint32_t stage_tx = uint32_t(nprod == 3 ? kStageBytes : kABytes + kBBytes);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long issued = 0;
+      for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
+        const int ch = w / ntiles, ti = w - ch * ntiles;
+        const int2 tl = tiles[ti];
+        const int kb0 = ch * kKB, kb1 = min(nkb_total, kb0 + kKB);
+        for (int kb = kb0; kb < kb1; ++kb, ++issued) {
+          const int s = int(issued % kGStages);
+          const uint32_t k = uint32_t(issued / kGStages);
+          if (!tc::mbar_wait(&bs->empty[s], (k & 1) ^ 1, kGSpin)) {
+            g_abort(bs, status);
+            break;
+          }
+          uint8_t* st = smem + s * kStageBytes;
+          tc::mbar_arrive_expect_tx(&bs->full[s], stage_tx);
+          tc::tma_load_2d(st, &tAh, &bs->full[s], kb * 64, tl.x * kGM);
+          tc::tma_load_2d(st + 2 * kABytes, &tBh, &bs->full[s], kb * 64, tl.y * kGN);
+          if (nprod == 3) {
+            tc::tma_load_2d(st + kABytes, &tAl, &bs->full[s], kb * 64, tl.x * kGM);
+            tc::tma_load_2d(st + 2 * kABytes + kBBytes, &tBl, &bs->full[s], kb * 64, tl.y * kGN);
+          }
+        }
+      }
+      if (g_aborted(bs))
+        for (long long x = issued > kGStages ? issued - kGStages : 0; x < issued; ++x)
+          tc::mbar_wait(&bs->full[x % kGStages], uint32_t(x / kGStages) & 1, kGSpin);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(kGM, kGN);
+      long long used = 0, accu = 0;
+      for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x, ++accu) {
+        const int ch = w / ntiles;
+        const int kb0 = ch * kKB, kb1 = min(nkb_total, kb0 + kKB);
+        const int b = int(accu & 1);
+        if (!tc::mbar_wait(&bs->acce[b], (uint32_t(accu >> 1) & 1) ^ 1, kGSpin)) {
+          g_abort(bs, status);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t d = tmem + uint32_t(b * kGN);
+        bool first = true;
+        for (int kb = kb0; kb < kb1; ++kb, ++used) {
+          const int s = int(used % kGStages);
+          if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kGStages) & 1, kGSpin)) {
+            g_abort(bs, status);
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t st = tc::smem_u32(smem + s * kStageBytes);
+          const uint32_t ah = st, al = st + kABytes, bh = st + 2 * kABytes, bl = bh + kBBytes;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, first ? 0u : 1u);
+            first = false;
+            if (nprod == 3) {
+              tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bl + ks * 32), idesc, 1u);
+              tc::mma_bf16(d, tc::sdesc_k128(al + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, 1u);
+            }
+          }
+          tc::mma_commit(&bs->empty[s]);
+        }
+        if (g_aborted(bs)) break;
+        tc::mma_commit(&bs->accf[b]);
+      }
+      tc::mma_commit(&bs->done);
+      tc::mbar_wait(&bs->done, 0, kGSpin);
+    }
+  } else {
+    // epilogue: thread = one tile row (TMEM lane), 256 FP32 columns
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    long long accu = 0;
+    for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x, ++accu) {
+      const int b = int(accu & 1);
+      if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kGSpin)) {
+        g_abort(bs, status);
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * kGN);
+      float4* dst = reinterpret_cast<float4*>(part + (int64_t(w) * kGM + row) * kGN);
+#pragma unroll 1
+      for (int c = 0; c < kGN / 32; ++c) {
+        uint32_t r[32];
+        __syncwarp();
+        tc::tmem_ld_32x32b_x32(taddr + c * 32, r);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          dst[c * 8 + e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]),
+                                       __uint_as_float(r[4 * e + 2]), __uint_as_float(r[4 * e + 3]));
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// S[a][c] = sum over chunks of the partial tile holding (min, max) (FP64).
+__global__ void gram_tc_combine_kernel(const float* __restrict__ part, const int* __restrict__ tile_of, int ntn,
+                                       int ntiles, int nchunks, int64_t p, double* __restrict__ S, int64_t lds,
+                                       int accumulate) {
+  const int64_t a = int64_t(blockIdx.y) * blockDim.y + threadIdx.y;
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (a >= p || c >= p) return;
+  const int64_t lo = min(a, c), hi = max(a, c);
+  const int ti = tile_of[(lo / kGM) * ntn + hi / kGN];
+  const int64_t off = (lo % kGM) * kGN + hi % kGN;
+  double s = 0.0;
+  for (int ch = 0; ch < nchunks; ++ch) s += double(part[(int64_t(ch) * ntiles + ti) * (kGM * kGN) + off]);
+  if (accumulate)
+    S[a * lds + c] += s;
+  else
+    S[a * lds + c] = s;
+}
+
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn g_encode() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+// X^T plane: p rows x ld_t bf16 (row-major), box boxrows x 64
+bool gmap(CUtensorMap* m, const void* base, int64_t p, int64_t ld_t, int boxrows) {
+  EncodeFn fn = g_encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cuuint64_t(ld_t), cuuint64_t(p)};
+  cuuint64_t strides[1] = {cuuint64_t(ld_t) * 2};
+  cuuint32_t box[2] = {64u, cuuint32_t(boxrows)};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct GramPlan {
+  int ntm, ntn, ntiles, nkb, nchunks;
+};
+
+GramPlan plan(const gmgm_matrix* m) {
+  GramPlan g;
+  const int64_t p = m->cols;
+  g.ntm = int((p + kGM - 1) / kGM);
+  g.ntn = int((p + kGN - 1) / kGN);
+  g.ntiles = 0;
+  for (int nt = 0; nt < g.ntn; ++nt)
+    for (int mt = 0; mt < g.ntm; ++mt)
+      if (int64_t(nt) * kGN + kGN - 1 >= int64_t(mt) * kGM) ++g.ntiles;
+  g.nkb = int(m->ld_t / 64);
+  g.nchunks = (g.nkb + kKB - 1) / kKB;
+  return g;
+}
+
+}  // namespace
+
+int gram_tc_splits(gmgm_handle*, const gmgm_matrix* m) { return plan(m).nchunks; }
+
+size_t gram_tc_scratch_bytes(const gmgm_matrix* m) {
+  GramPlan g = plan(m);
+  return Carve::round(size_t(g.nchunks) * g.ntiles * kGM * kGN * 4) + Carve::round(size_t(g.ntiles) * 8) +
+         Carve::round(size_t(g.ntm) * g.ntn * 4) + 4096;
+}
+
+cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec, double* S, int64_t lds,
+                           int accumulate, float* scratch, int /*splits*/) {
+  GramPlan g = plan(m);
+  Carve c(scratch);
+  float* part = c.take<float>(size_t(g.nchunks) * g.ntiles * kGM * kGN);
+  int2* tiles = c.take<int2>(g.ntiles);
+  int* tile_of = c.take<int>(size_t(g.ntm) * g.ntn);
+  // tile list (host-built, small) and its inverse map
+  std::vector<int2> ht;
+  std::vector<int> hof(size_t(g.ntm) * g.ntn, -1);
+  for (int nt = 0; nt < g.ntn; ++nt)
+    for (int mt = 0; mt < g.ntm; ++mt)
+      if (int64_t(nt) * kGN + kGN - 1 >= int64_t(mt) * kGM) {
+        hof[size_t(mt) * g.ntn + nt] = int(ht.size());
+        ht.push_back(make_int2(mt, nt));
+      }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(tiles, ht.data(), ht.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(tile_of, hof.data(), hof.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream)) !=
+      cudaSuccess)
+    return e;
+  // the host vectors must outlive the async copies
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return e;
+  const int nprod = prec == GMGM_BF16X3 ? 3 : 1;
+  CUtensorMap ah, al, bh, bl;
+  const void* lo = m->xt_lo ? m->xt_lo : m->xt_hi;
+  if (!gmap(&ah, m->xt_hi, m->cols, m->ld_t, kGM) || !gmap(&al, lo, m->cols, m->ld_t, kGM) ||
+      !gmap(&bh, m->xt_hi, m->cols, m->ld_t, kGN) || !gmap(&bl, lo, m->cols, m->ld_t, kGN))
+    return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kGSmem))) !=
+      cudaSuccess)
+    return e;
+  const int items = g.ntiles * g.nchunks;
+  const int grid = std::min(items, h->num_sms);
+  gram_tc_kernel<<<grid, kGThreads, kGSmem, h->stream>>>(ah, al, bh, bl, tiles, g.ntiles, g.nkb, g.nchunks, nprod,
+                                                         part, h->d_status);
+  dim3 cb(32, 8), cg(unsigned((m->cols + 31) / 32), unsigned((m->cols + 7) / 8));
+  gram_tc_combine_kernel<<<cg, cb, 0, h->stream>>>(part, tile_of, g.ntn, g.ntiles, g.nchunks, m->cols, S, lds,
+                                                   accumulate);
+  note_launch(2);
+  return cudaGetLastError();
 }
 
 }  // namespace gmgm

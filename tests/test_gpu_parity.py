@@ -51,6 +51,33 @@ def test_gram_fp32_cols(g, cuda_dev, n, p):
     assert np.array_equal(S, S.T)
 
 
+def _split_planes(x, dev):
+    """BF16 hi/lo planes of X^T (p x ld_t, zero padded), as the preprocessing
+    kernel lays them out."""
+    n, p = x.shape
+    ld_t = ((n + 63) // 64) * 64
+    xt = torch.zeros(p, ld_t, dtype=torch.float32, device=dev)
+    xt[:, :n] = torch.from_numpy(x).to(dev).T
+    hi = xt.to(torch.bfloat16)
+    lo = (xt - hi.float()).to(torch.bfloat16)
+    return hi.contiguous(), lo.contiguous(), ld_t
+
+
+@pytest.mark.parametrize("n,p", [(5000, 300), (20000, 2000), (70, 5), (9000, 129)])
+def test_gram_tensor_core_3xbf16(g, cuda_dev, n, p):
+    x = _rng(11 + p).standard_normal((n, p)).astype(np.float32)
+    hi, lo, ld_t = _split_planes(x, cuda_dev)
+    ref = og.gram(x.astype(np.float64), 1)
+    S3 = g.gram(None, g.SIDE_COLS, g.BF16X3, xt_hi=hi, xt_lo=lo, ld_t=ld_t, rows=n, cols=p).cpu().numpy()
+    err3 = np.max(np.abs(S3 - ref)) / np.abs(ref).max()
+    assert err3 <= 2e-5, err3
+    assert np.array_equal(S3, S3.T)
+    S1 = g.gram(None, g.SIDE_COLS, g.BF16, xt_hi=hi, ld_t=ld_t, rows=n, cols=p).cpu().numpy()
+    err1 = np.max(np.abs(S1 - ref)) / np.abs(ref).max()
+    assert err1 <= 2e-2, err1
+    assert err3 < err1
+
+
 def test_gram_rows_and_tensor_axes(g, cuda_dev):
     t = _rng(2).standard_normal((7, 40, 33)).astype(np.float32)
     tt = torch.from_numpy(t).to(cuda_dev)
