@@ -159,7 +159,7 @@ int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec, do
     if (((uintptr_t)m->xt_hi % 16) || (m->xt_lo && ((uintptr_t)m->xt_lo % 16)))
       return fail(h, GMGM_E_ARG, "gmgm_gram: xt buffers must be 16-byte aligned");
     int splits = gmgm::gram_tc_splits(h, m);
-    int rc = gmgm::ensure_scratch(h, gmgm::gram_tc_scratch_bytes(m));
+    int rc = gmgm::ensure_scratch(h, gmgm::gram_tc_scratch_bytes(h, m));
     if (rc) return rc;
     GMGM_CUDA_TRY(h, gmgm::launch_gram_tc(h, m, prec, S, lds, accumulate,
                                           static_cast<float*>(h->scratch), splits));

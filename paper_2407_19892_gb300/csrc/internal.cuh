@@ -72,7 +72,7 @@ size_t gram_fp32_scratch_bytes(int64_t dS, int splits);
 cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec, double* S,
                            int64_t lds, int accumulate, float* partials, int splits);
 int gram_tc_splits(gmgm_handle* h, const gmgm_matrix* m);
-size_t gram_tc_scratch_bytes(const gmgm_matrix* m);
+size_t gram_tc_scratch_bytes(gmgm_handle* h, const gmgm_matrix* m);
 
 size_t eig_scratch_bytes(int64_t d, int32_t r);
 cudaError_t launch_eig(gmgm_handle* h, int64_t d, const double* S, int64_t lds, int32_t r,

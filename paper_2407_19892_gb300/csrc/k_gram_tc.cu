@@ -6,14 +6,16 @@
 // product); plain BF16 forms hi.hi^T only.
 //
 // Work item = (output tile 128 genes x 256 genes of the upper triangle,
-// chunk of kKB 64-cell K blocks).  Persistent CTAs, warp-specialised:
+// K range of the cells).  The tensor core's FP32 accumulation is kept short:
+// the accumulator is drained every kSub K blocks (2048 cells) into an FP64
+// running tile owned by the CTA.  Persistent CTAs, warp-specialised:
 //   warp 0      TMA producer: per K block the A (128 rows) and B (256 rows)
 //               slices of hi (and lo) into a 2-stage ring;
 //   warp 1      MMA issuer: tcgen05.mma M=128 N=256 K=16, FP32 accumulator
 //               in TMEM (double-buffered, 2 x 256 columns);
-//   warps 2-5   epilogue: tcgen05.ld the accumulator, store the FP32 partial
-//               tile; a second kernel sums the chunks in FP64 and writes both
-//               triangles of S.
+//   warps 2-5   epilogue: tcgen05.ld each drained accumulator and add it to
+//               the item's FP64 tile; a second kernel sums the K ranges in
+//               FP64 and writes both triangles of S.
 // Every wait is bounded (GMGM_DEV_TIMEOUT on expiry, TMEM freed on exit).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -31,7 +33,7 @@ namespace {
 
 constexpr int kGM = 128;                     // tile rows (genes a)
 constexpr int kGN = 256;                     // tile cols (genes b)
-constexpr int kKB = 128;                     // 64-cell K blocks per work item (8192 cells)
+constexpr int kSub = 32;                     // 64-cell K blocks per accumulator drain
 constexpr int kGStages = 2;
 constexpr int kGThreads = 64 + 128;
 constexpr int kABytes = kGM * 128;           // 16 KB per plane
@@ -62,8 +64,8 @@ __device__ __forceinline__ void g_abort(GBars* bs, int* status) {
 __global__ void __launch_bounds__(kGThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                    const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
-                   const int2* __restrict__ tiles, int ntiles, int nkb_total, int nchunks, int nprod,
-                   float* __restrict__ part, int* __restrict__ status) {
+                   const int2* __restrict__ tiles, int ntiles, int nkb_total, int nsplit, int nprod,
+                   double* __restrict__ part, int* __restrict__ status) {
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   GBars* bs = reinterpret_cast<GBars*>(smem + kGStages * kStageBytes);
@@ -79,7 +81,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = bs->tmem_base;
-  const int items = ntiles * nchunks;
+  const int items = ntiles * nsplit;
+  const int kb_per = (nkb_total + nsplit - 1) / nsplit;
   const uint32_t stage_tx = uint32_t(nprod == 3 ? kStageBytes : kABytes + kBBytes);
 
   if (warp == 0) {
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
         const int ch = w / ntiles, ti = w - ch * ntiles;
         const int2 tl = tiles[ti];
-        const int kb0 = ch * kKB, kb1 = min(nkb_total, kb0 + kKB);
+        const int kb0 = ch * kb_per, kb1 = min(nkb_total, kb0 + kb_per);
         for (int kb = kb0; kb < kb1; ++kb, ++issued) {
           const int s = int(issued % kGStages);
           const uint32_t k = uint32_t(issued / kGStages);
@@ -114,39 +117,42 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(kGM, kGN);
       long long used = 0, accu = 0;
-      for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x, ++accu) {
+      for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
         const int ch = w / ntiles;
-        const int kb0 = ch * kKB, kb1 = min(nkb_total, kb0 + kKB);
-        const int b = int(accu & 1);
-        if (!tc::mbar_wait(&bs->acce[b], (uint32_t(accu >> 1) & 1) ^ 1, kGSpin)) {
-          g_abort(bs, status);
-          break;
-        }
-        tc::fence_after_sync();
-        const uint32_t d = tmem + uint32_t(b * kGN);
-        bool first = true;
-        for (int kb = kb0; kb < kb1; ++kb, ++used) {
-          const int s = int(used % kGStages);
-          if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kGStages) & 1, kGSpin)) {
+        const int kb0 = ch * kb_per, kb1 = min(nkb_total, kb0 + kb_per);
+        for (int sb = kb0; sb < kb1 && !g_aborted(bs); sb += kSub, ++accu) {
+          const int b = int(accu & 1);
+          if (!tc::mbar_wait(&bs->acce[b], (uint32_t(accu >> 1) & 1) ^ 1, kGSpin)) {
             g_abort(bs, status);
             break;
           }
           tc::fence_after_sync();
-          const uint32_t st = tc::smem_u32(smem + s * kStageBytes);
-          const uint32_t ah = st, al = st + kABytes, bh = st + 2 * kABytes, bl = bh + kBBytes;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, first ? 0u : 1u);
-            first = false;
-            if (nprod == 3) {
-              tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bl + ks * 32), idesc, 1u);
-              tc::mma_bf16(d, tc::sdesc_k128(al + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, 1u);
+          const uint32_t d = tmem + uint32_t(b * kGN);
+          bool first = true;
+          const int se = min(kb1, sb + kSub);
+          for (int kb = sb; kb < se; ++kb, ++used) {
+            const int s = int(used % kGStages);
+            if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kGStages) & 1, kGSpin)) {
+              g_abort(bs, status);
+              break;
             }
+            tc::fence_after_sync();
+            const uint32_t st = tc::smem_u32(smem + s * kStageBytes);
+            const uint32_t ah = st, al = st + kABytes, bh = st + 2 * kABytes, bl = bh + kBBytes;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, first ? 0u : 1u);
+              first = false;
+              if (nprod == 3) {
+                tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bl + ks * 32), idesc, 1u);
+                tc::mma_bf16(d, tc::sdesc_k128(al + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, 1u);
+              }
+            }
+            tc::mma_commit(&bs->empty[s]);
           }
-          tc::mma_commit(&bs->empty[s]);
+          if (g_aborted(bs)) break;
+          tc::mma_commit(&bs->accf[b]);
         }
-        if (g_aborted(bs)) break;
-        tc::mma_commit(&bs->accf[b]);
       }
       tc::mma_commit(&bs->done);
       tc::mbar_wait(&bs->done, 0, kGSpin);
@@ -156,29 +162,40 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     long long accu = 0;
-    for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x, ++accu) {
-      const int b = int(accu & 1);
-      if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kGSpin)) {
-        g_abort(bs, status);
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * kGN);
-      float4* dst = reinterpret_cast<float4*>(part + (int64_t(w) * kGM + row) * kGN);
+    for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
+      const int ch = w / ntiles;
+      const int kb0 = ch * kb_per, kb1 = min(nkb_total, kb0 + kb_per);
+      double2* dst = reinterpret_cast<double2*>(part + (int64_t(w) * kGM + row) * kGN);
+      for (int sb = kb0; sb < kb1 && !g_aborted(bs); sb += kSub, ++accu) {
+        const int b = int(accu & 1);
+        if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kGSpin)) {
+          g_abort(bs, status);
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * kGN);
+        const bool init = sb == kb0;
 #pragma unroll 1
-      for (int c = 0; c < kGN / 32; ++c) {
-        uint32_t r[32];
-        __syncwarp();
-        tc::tmem_ld_32x32b_x32(taddr + c * 32, r);
-        tc::tmem_ld_wait();
+        for (int c = 0; c < kGN / 32; ++c) {
+          uint32_t r[32];
+          __syncwarp();
+          tc::tmem_ld_32x32b_x32(taddr + c * 32, r);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          dst[c * 8 + e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]),
-                                       __uint_as_float(r[4 * e + 2]), __uint_as_float(r[4 * e + 3]));
+          for (int e = 0; e < 16; ++e) {
+            double2 v = make_double2(double(__uint_as_float(r[2 * e])), double(__uint_as_float(r[2 * e + 1])));
+            if (!init) {
+              const double2 o = dst[c * 16 + e];
+              v.x += o.x;
+              v.y += o.y;
+            }
+            dst[c * 16 + e] = v;
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
     }
   }
   __syncthreads();
@@ -188,9 +205,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
   }
 }
 
-// S[a][c] = sum over chunks of the partial tile holding (min, max) (FP64).
-__global__ void gram_tc_combine_kernel(const float* __restrict__ part, const int* __restrict__ tile_of, int ntn,
-                                       int ntiles, int nchunks, int64_t p, double* __restrict__ S, int64_t lds,
+// S[a][c] = sum over K ranges of the partial tile holding (min, max) (FP64).
+__global__ void gram_tc_combine_kernel(const double* __restrict__ part, const int* __restrict__ tile_of, int ntn,
+                                       int ntiles, int nsplit, int64_t p, double* __restrict__ S, int64_t lds,
                                        int accumulate) {
   const int64_t a = int64_t(blockIdx.y) * blockDim.y + threadIdx.y;
   const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -199,7 +216,7 @@ __global__ void gram_tc_combine_kernel(const float* __restrict__ part, const int
   const int ti = tile_of[(lo / kGM) * ntn + hi / kGN];
   const int64_t off = (lo % kGM) * kGN + hi % kGN;
   double s = 0.0;
-  for (int ch = 0; ch < nchunks; ++ch) s += double(part[(int64_t(ch) * ntiles + ti) * (kGM * kGN) + off]);
+  for (int ch = 0; ch < nsplit; ++ch) s += part[(int64_t(ch) * ntiles + ti) * (kGM * kGN) + off];
   if (accumulate)
     S[a * lds + c] += s;
   else
@@ -236,10 +253,10 @@ bool gmap(CUtensorMap* m, const void* base, int64_t p, int64_t ld_t, int boxrows
 }
 
 struct GramPlan {
-  int ntm, ntn, ntiles, nkb, nchunks;
+  int ntm, ntn, ntiles, nkb, nsplit;
 };
 
-GramPlan plan(const gmgm_matrix* m) {
+GramPlan plan(const gmgm_matrix* m, int num_sms) {
   GramPlan g;
   const int64_t p = m->cols;
   g.ntm = int((p + kGM - 1) / kGM);
@@ -249,25 +266,27 @@ GramPlan plan(const gmgm_matrix* m) {
     for (int mt = 0; mt < g.ntm; ++mt)
       if (int64_t(nt) * kGN + kGN - 1 >= int64_t(mt) * kGM) ++g.ntiles;
   g.nkb = int(m->ld_t / 64);
-  g.nchunks = (g.nkb + kKB - 1) / kKB;
+  // K ranges per tile: enough work items to cover the SMs, each range at
+  // least one drain long
+  g.nsplit = std::max(1, std::min((num_sms + g.ntiles / 2) / g.ntiles, (g.nkb + kSub - 1) / kSub));
   return g;
 }
 
 }  // namespace
 
-int gram_tc_splits(gmgm_handle*, const gmgm_matrix* m) { return plan(m).nchunks; }
+int gram_tc_splits(gmgm_handle* h, const gmgm_matrix* m) { return plan(m, h->num_sms).nsplit; }
 
-size_t gram_tc_scratch_bytes(const gmgm_matrix* m) {
-  GramPlan g = plan(m);
-  return Carve::round(size_t(g.nchunks) * g.ntiles * kGM * kGN * 4) + Carve::round(size_t(g.ntiles) * 8) +
+size_t gram_tc_scratch_bytes(gmgm_handle* h, const gmgm_matrix* m) {
+  GramPlan g = plan(m, h->num_sms);
+  return Carve::round(size_t(g.nsplit) * g.ntiles * kGM * kGN * 8) + Carve::round(size_t(g.ntiles) * 8) +
          Carve::round(size_t(g.ntm) * g.ntn * 4) + 4096;
 }
 
 cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec, double* S, int64_t lds,
                            int accumulate, float* scratch, int /*splits*/) {
-  GramPlan g = plan(m);
+  GramPlan g = plan(m, h->num_sms);
   Carve c(scratch);
-  float* part = c.take<float>(size_t(g.nchunks) * g.ntiles * kGM * kGN);
+  double* part = c.take<double>(size_t(g.nsplit) * g.ntiles * kGM * kGN);
   int2* tiles = c.take<int2>(g.ntiles);
   int* tile_of = c.take<int>(size_t(g.ntm) * g.ntn);
   // tile list (host-built, small) and its inverse map
@@ -297,12 +316,12 @@ cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec,
   if ((e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kGSmem))) !=
       cudaSuccess)
     return e;
-  const int items = g.ntiles * g.nchunks;
+  const int items = g.ntiles * g.nsplit;
   const int grid = std::min(items, h->num_sms);
-  gram_tc_kernel<<<grid, kGThreads, kGSmem, h->stream>>>(ah, al, bh, bl, tiles, g.ntiles, g.nkb, g.nchunks, nprod,
+  gram_tc_kernel<<<grid, kGThreads, kGSmem, h->stream>>>(ah, al, bh, bl, tiles, g.ntiles, g.nkb, g.nsplit, nprod,
                                                          part, h->d_status);
   dim3 cb(32, 8), cg(unsigned((m->cols + 31) / 32), unsigned((m->cols + 7) / 8));
-  gram_tc_combine_kernel<<<cg, cb, 0, h->stream>>>(part, tile_of, g.ntn, g.ntiles, g.nchunks, m->cols, S, lds,
+  gram_tc_combine_kernel<<<cg, cb, 0, h->stream>>>(part, tile_of, g.ntn, g.ntiles, g.nsplit, m->cols, S, lds,
                                                    accumulate);
   note_launch(2);
   return cudaGetLastError();
