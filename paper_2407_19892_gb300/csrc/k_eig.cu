@@ -1,14 +1,14 @@
 // FP64 symmetric eigendecomposition on the GPU (the small axis Gram, e.g.
 // 2000 x 2000 genes).  Steps:
 //   1. Householder tridiagonalisation Q^T S Q = T, one cooperative kernel with
-//      two bounded grid barriers per reflector (matrix in L2, FP64 bound);
-//   2. bisection with Sturm counts for the wanted eigenvalues of T (one
-//      thread per eigenvalue);
+//      one bounded grid barrier per reflector (matrix in L2, FP64 bound);
+//   2. multisection with division-free Sturm counts for the wanted
+//      eigenvalues of T (eight lanes per eigenvalue);
 //   3. inverse iteration on T - lambda I (tridiagonal LU with partial
 //      pivoting, one thread per eigenvalue), then modified Gram-Schmidt inside
 //      clusters of nearly equal eigenvalues;
-//   4. back-transformation Z <- Q Z (one warp per eigenvector, reflectors
-//      streamed from L2);
+//   4. back-transformation Z <- Q Z (one warp per two eigenvectors,
+//      reflectors streamed from L2);
 //   5. output: the r largest eigenvalues descending, vectors row-major d x r.
 #include <cuda_runtime.h>
 
@@ -32,81 +32,126 @@ __global__ void copy_sym_kernel(const double* __restrict__ S, int64_t lds, int n
   A[i * n + j] = i >= j ? S[i * lds + j] : S[j * lds + i];
 }
 
-__global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, double* dv, double* ev,
-                                                              double* Vh, double* tau, double* P,
-                                                              unsigned* bar, int* status) {
+// Householder of x (length m, in smem): v (v[0] = 1) and tau with
+// (I - tau v v^T) x = beta e_0.  Every CTA runs it on identical data.
+__device__ __forceinline__ void householder(double* x, int m, double* red, double& tau, double& beta) {
+  double ss = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) ss += x[i] * x[i];
+  const double tail = block_sum(ss, red);
+  const double x0 = x[0];
+  tau = 0.0;
+  beta = x0;
+  if (tail > 0.0) {
+    const double nrm = sqrt(x0 * x0 + tail);
+    beta = x0 >= 0.0 ? -nrm : nrm;
+    tau = (beta - x0) / beta;
+    const double sc = 1.0 / (x0 - beta);
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= sc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) x[0] = 1.0;
+  __syncthreads();
+}
+
+// Tridiagonalisation with one grid barrier per reflector: the rank-2 update
+// of step k and the mat-vec of step k+1 share one pass over the trailing
+// matrix.  Row k+1 of the updated matrix (which defines reflector k+1) is
+// formed redundantly by every CTA from row k+1 of the old matrix.
+//   v = reflector k (rows/cols k+1..n-1), u = reflector k+1 (k+2..n-1),
+//   P = tau_{k+1} A_{k+1} u (written by row owners, read after the barrier;
+//   double-buffered so a CTA still reading step k's P never sees step k+1's).
+__global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, double* dv, double* ev, double* Vh,
+                                                              double* tau_out, double* P, unsigned* bar,
+                                                              int* status) {
   extern __shared__ double sm[];
-  double* v = sm;
-  double* w = sm + n;
+  double* v = sm;          // [n]
+  double* w = sm + n;      // [n]
+  double* u = sm + 2 * n;  // [n]
   __shared__ double red[33];
   const unsigned nb = gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int gwarp = blockIdx.x * nwarps + warp, total_warps = nb * nwarps;
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;
-    const double* rowk = A + int64_t(k) * n + k + 1;
-    double ss = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      double t = __ldcg(rowk + i);
-      v[i] = t;
-      if (i > 0) ss += t * t;
-    }
-    const double tail = block_sum(ss, red);  // syncs: v visible
-    const double x0 = v[0];
-    double tk = 0.0, beta = x0;
-    if (tail > 0.0) {
-      const double nrm = sqrt(x0 * x0 + tail);
-      beta = x0 >= 0.0 ? -nrm : nrm;
-      tk = (beta - x0) / beta;
-      const double sc = 1.0 / (x0 - beta);
-      for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) v[i] *= sc;
-    }
+  // prologue: reflector 0 from row 0, P = tau_0 A[1:,1:] v
+  double tk, beta;
+  {
+    const int m = n - 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = __ldcg(A + 1 + i);
     __syncthreads();
-    if (threadIdx.x == 0) v[0] = 1.0;
-    __syncthreads();
+    householder(v, m, red, tk, beta);
     if (blockIdx.x == 0) {
       if (threadIdx.x == 0) {
-        dv[k] = __ldcg(A + int64_t(k) * n + k);
-        ev[k] = beta;
-        tau[k] = tk;
+        dv[0] = __ldcg(A);
+        ev[0] = beta;
+        tau_out[0] = tk;
       }
-      for (int i = threadIdx.x; i < m; i += blockDim.x) Vh[int64_t(k) * n + k + 1 + i] = v[i];
+      for (int i = threadIdx.x; i < m; i += blockDim.x) Vh[1 + i] = v[i];
     }
-    if (tk == 0.0) continue;  // identical decision in every CTA (same data)
-    // p = tau * A_sub v, one warp per row
     for (int i = gwarp; i < m; i += total_warps) {
-      const double* row = A + int64_t(k + 1 + i) * n + k + 1;
+      const double* row = A + int64_t(1 + i) * n + 1;
       double s = 0.0;
       for (int j = lane; j < m; j += 32) s += __ldcg(row + j) * v[j];
       s = warp_sum(s);
       if (lane == 0) P[i] = tk * s;
     }
     if (!grid_barrier(bar, nb, status)) return;
+  }
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // size of the trailing block of step k
+    // w = P - K v, K = tau_k (P.v) / 2
     double pv = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) pv += __ldcg(P + i) * v[i];
+    const double* Pc = P + (k & 1) * int64_t(n);
+    double* Pn = P + ((k + 1) & 1) * int64_t(n);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) pv += __ldcg(Pc + i) * v[i];
     pv = block_sum(pv, red);
     const double K = 0.5 * tk * pv;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = __ldcg(P + i) - K * v[i];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = tk != 0.0 ? __ldcg(Pc + i) - K * v[i] : 0.0;
     __syncthreads();
-    // A_sub -= v w^T + w v^T over (row, 128-column segment) work items
-    const int segs = (m + kSeg - 1) / kSeg;
-    const int64_t items = int64_t(m) * segs;
-    for (int64_t it = gwarp; it < items; it += total_warps) {
-      const int i = int(it / segs), sg = int(it - int64_t(i) * segs);
-      double* row = A + int64_t(k + 1 + i) * n + k + 1;
-      const double vi = v[i], wi = w[i];
-      const int j1 = min(m, (sg + 1) * kSeg);
-      for (int j = sg * kSeg + lane; j < j1; j += 32) row[j] = __ldcg(row + j) - (vi * w[j] + wi * v[j]);
+    // row k+1 of the updated matrix, columns k+1..n-1 -> u[0..m-1]
+    {
+      const double* row = A + int64_t(k + 1) * n + k + 1;
+      const double v0 = v[0], w0 = w[0];
+      for (int j = threadIdx.x; j < m; j += blockDim.x) u[j] = __ldcg(row + j) - (v0 * w[j] + w0 * v[j]);
     }
+    __syncthreads();
+    const double dnext = u[0];
+    double tn = 0.0, bn = 0.0;
+    const bool more = k + 3 < n;  // a reflector k+1 exists
+    if (more) {
+      householder(u + 1, m - 1, red, tn, bn);  // u+1 holds x = row entries k+2..n-1
+    } else {
+      bn = u[1];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      dv[k + 1] = dnext;
+      ev[k + 1] = bn;
+      if (more) tau_out[k + 1] = tn;
+    }
+    if (more && blockIdx.x == 0)
+      for (int i = threadIdx.x; i < m - 1; i += blockDim.x) Vh[int64_t(k + 1) * n + k + 2 + i] = u[1 + i];
+    // fused pass: rows i, cols j in k+2..n-1 (local index t = i - (k+1) >= 1)
+    const int segs = (m - 1 + kSeg - 1) / kSeg;
+    for (int it = gwarp; it < (m - 1); it += total_warps) {
+      const int t = 1 + it;
+      double* row = A + int64_t(k + 1 + t) * n + k + 2;
+      const double vi = v[t], wi = w[t];
+      double s = 0.0;
+      for (int sg = 0; sg < segs; ++sg) {
+        const int j1 = min(m - 1, (sg + 1) * kSeg);
+        for (int jj = sg * kSeg + lane; jj < j1; jj += 32) {
+          const double a = tk != 0.0 ? __ldcg(row + jj) - (vi * w[1 + jj] + wi * v[1 + jj]) : __ldcg(row + jj);
+          if (tk != 0.0) row[jj] = a;
+          s += a * u[1 + jj];
+        }
+      }
+      s = warp_sum(s);
+      if (lane == 0 && more) Pn[it] = tn * s;
+    }
+    // next step's reflector
+    for (int i = threadIdx.x; i < m - 1; i += blockDim.x) v[i] = u[1 + i];
+    tk = tn;
     if (!grid_barrier(bar, nb, status)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (n >= 2) {
-      dv[n - 2] = __ldcg(A + int64_t(n - 2) * n + n - 2);
-      ev[n - 2] = __ldcg(A + int64_t(n - 2) * n + n - 1);
-    }
-    dv[n - 1] = __ldcg(A + int64_t(n - 1) * n + n - 1);
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) dv[n - 1] = __ldcg(A + int64_t(n - 1) * n + n - 1);
 }
 
 __global__ void tiny_tridiag_kernel(const double* A, int n, double* dv, double* ev) {
@@ -145,23 +190,39 @@ __global__ void tri_info_kernel(const double* dv, const double* ev, int n, doubl
   }
 }
 
-// number of eigenvalues of T strictly below x (Sturm count of the LDL^T pivots)
-__device__ __forceinline__ int sturm_count(const double* dv, const double* e2, int n, double x,
-                                           double pivmin) {
-  double q = dv[0] - x;
-  int cnt = q < 0.0;
-  if (fabs(q) < pivmin) q = -pivmin;
+// Number of eigenvalues of T strictly below x: sign changes of the Sturm
+// sequence P_i = (d_i - x) P_{i-1} - e_{i-1}^2 P_{i-2} (P_{-1} = 1), i.e.
+// the leading principal minors of T - xI.  Division-free; rescaled by powers
+// of two (exact) to stay in range; a zero takes the opposite sign of its
+// predecessor.
+__device__ __forceinline__ int sturm_count(const double* dv, const double* e2, int n, double x) {
+  double pm = 1.0, p = dv[0] - x;
+  int sp = p < 0.0 || p == 0.0;
+  int cnt = sp;
   for (int i = 1; i < n; ++i) {
-    q = dv[i] - x - e2[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    const double pn = (dv[i] - x) * p - e2[i - 1] * pm;
+    const int sn = pn < 0.0 || (pn == 0.0 && !sp);
+    cnt += sn ^ sp;
+    pm = p;
+    p = pn;
+    sp = sn;
+    const double ap = fabs(p);
+    if (ap > 0x1p+480 || (ap < 0x1p-480 && ap != 0.0)) {
+      const int e = ilogb(p);
+      p = scalbn(p, -e);
+      pm = scalbn(pm, -e);
+    }
   }
   return cnt;
 }
 
-// Thread t finds the ascending eigenvalue of index j0 + t by bisection.
-__global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __restrict__ e2_g, int n,
-                              int j0, int cnt, const double* __restrict__ info, double* __restrict__ lam) {
+constexpr int kMS = 8;  // lanes per eigenvalue (9-way multisection)
+
+// Lanes in groups of kMS find the ascending eigenvalues j0 + group: each
+// round evaluates kMS interior points of the current interval and keeps the
+// sub-interval holding eigenvalue j (counts are monotone in x).
+__global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __restrict__ e2_g, int n, int j0,
+                              int cnt, const double* __restrict__ info, double* __restrict__ lam) {
   extern __shared__ double sm[];
   double* dv = sm;
   double* e2 = sm + n;
@@ -170,21 +231,28 @@ __global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __r
     if (i + 1 < n) e2[i] = e2_g[i];
   }
   __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  const int j = j0 + t;
-  const double pivmin = info[2];
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % kMS, gbase = lane - sub;
+  const int group = (blockIdx.x * blockDim.x + threadIdx.x) / kMS;
+  const bool active = group < cnt;
+  const int j = j0 + (active ? group : cnt - 1);
+  const double floor_abs = 4.0 * info[2];
   double lo = info[0], hi = info[1];
-  for (int it = 0; it < 256; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin || mid == lo || mid == hi)
-      break;
-    if (sturm_count(dv, e2, n, mid, pivmin) <= j)
-      lo = mid;
-    else
-      hi = mid;
+  for (int round = 0; round < 64; ++round) {
+    const bool done = hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + floor_abs;
+    if (!__any_sync(0xffffffffu, !done)) break;
+    const double x = lo + (hi - lo) * double(sub + 1) / double(kMS + 1);
+    const int c = sturm_count(dv, e2, n, x);
+    const unsigned bal = __ballot_sync(0xffffffffu, c <= j);
+    const int t = __popc((bal >> gbase) & ((1u << kMS) - 1));  // points with count <= j (a prefix)
+    const double xl = __shfl_sync(0xffffffffu, x, gbase + (t > 0 ? t - 1 : 0));
+    const double xh = __shfl_sync(0xffffffffu, x, gbase + (t < kMS ? t : kMS - 1));
+    if (!done) {
+      if (t > 0) lo = xl;
+      if (t < kMS) hi = xh;
+    }
   }
-  lam[t] = 0.5 * (lo + hi);
+  if (active && sub == 0) lam[group] = 0.5 * (lo + hi);
 }
 
 __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b) {
@@ -319,29 +387,53 @@ __global__ void cluster_mgs_kernel(const double* __restrict__ lam, int cnt, cons
   }
 }
 
-// Z <- H_0 H_1 ... H_{n-3} Z, H_k = I - tau_k v_k v_k^T; one warp per
-// eigenvector, the vector held in shared memory.
+// Z <- H_0 H_1 ... H_{n-3} Z, H_k = I - tau_k v_k v_k^T.  One warp holds two
+// eigenvectors in shared memory, so each reflector read from L2 serves both
+// and the two dot products overlap.
 __global__ void back_transform_kernel(const double* __restrict__ Vh, const double* __restrict__ tau, int n,
                                       int cnt, double* __restrict__ Zc) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int t = blockIdx.x * nwarps + warp;
-  if (t >= cnt) return;
-  double* z = sm + int64_t(warp) * n;
-  double* zg = Zc + int64_t(t) * n;
-  for (int i = lane; i < n; i += 32) z[i] = zg[i];
+  const int t0 = (blockIdx.x * nwarps + warp) * 2;
+  if (t0 >= cnt) return;
+  const bool two = t0 + 1 < cnt;
+  double* z0 = sm + int64_t(warp) * 2 * n;
+  double* z1 = z0 + n;
+  double* g0 = Zc + int64_t(t0) * n;
+  double* g1 = g0 + n;
+  for (int i = lane; i < n; i += 32) {
+    z0[i] = g0[i];
+    z1[i] = two ? g1[i] : 0.0;
+  }
   __syncwarp();
   for (int k = n - 3; k >= 0; --k) {
     const double tk = tau[k];
     if (tk == 0.0) continue;
     const double* vk = Vh + int64_t(k) * n;
-    double y = 0.0;
-    for (int i = k + 1 + lane; i < n; i += 32) y += __ldg(vk + i) * z[i];
-    y = warp_sum(y) * tk;
-    for (int i = k + 1 + lane; i < n; i += 32) z[i] -= y * __ldg(vk + i);
+    double y0 = 0.0, y1 = 0.0;
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const double vv = __ldg(vk + i);
+      y0 += vv * z0[i];
+      y1 += vv * z1[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+      y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    }
+    y0 *= tk;
+    y1 *= tk;
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const double vv = __ldg(vk + i);
+      z0[i] -= y0 * vv;
+      z1[i] -= y1 * vv;
+    }
     __syncwarp();
   }
-  for (int i = lane; i < n; i += 32) zg[i] = z[i];
+  for (int i = lane; i < n; i += 32) {
+    g0[i] = z0[i];
+    if (two) g1[i] = z1[i];
+  }
 }
 
 // evals[c] = lam[cnt-1-c]; evecs[i*ldv + c] = Zc[(cnt-1-c)*n + i]
@@ -380,7 +472,7 @@ EigScratch carve_eig(void* base, int64_t d, int32_t r) {
   s.dv = c.take<double>(d);
   s.ev = c.take<double>(d);
   s.e2 = c.take<double>(d);
-  s.P = c.take<double>(d);
+  s.P = c.take<double>(2 * d);
   s.info = c.take<double>(8);
   s.lam = c.take<double>(r);
   s.u0 = c.take<double>(d * B);
@@ -410,7 +502,7 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
   if ((e = cudaMemsetAsync(s.tau, 0, size_t(n) * sizeof(double), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(s.ev, 0, size_t(n) * sizeof(double), st)) != cudaSuccess) return e;
   if (n >= 3) {
-    const size_t smem = size_t(2) * n * sizeof(double);
+    const size_t smem = size_t(3) * n * sizeof(double);
     if ((e = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) !=
         cudaSuccess)
       return e;
@@ -419,7 +511,7 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
         cudaSuccess)
       return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    unsigned blocks = unsigned(h->num_sms) * unsigned(std::min(per_sm, 2));
+    unsigned blocks = unsigned(h->num_sms);
     // small problems: fewer CTAs (cheaper barriers)
     const unsigned want = unsigned((int64_t(n) * n + 16383) / 16384);
     blocks = std::min(blocks, std::max(1u, want));
@@ -444,8 +536,9 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
     if ((e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) !=
         cudaSuccess)
       return e;
-    const int tpb = 64;
-    bisect_kernel<<<unsigned((r + tpb - 1) / tpb), tpb, smem, st>>>(s.dv, s.e2, n, j0, r, s.info, s.lam);
+    const int tpb = 64;  // small blocks: the groups spread over every SM
+    const int64_t threads = int64_t(r) * kMS;
+    bisect_kernel<<<unsigned((threads + tpb - 1) / tpb), tpb, smem, st>>>(s.dv, s.e2, n, j0, r, s.info, s.lam);
   }
   const int B = std::min(r, kInvBatch);
   for (int t0 = 0; t0 < r; t0 += B) {
@@ -457,12 +550,12 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
   }
   cluster_mgs_kernel<<<unsigned(r), 256, 0, st>>>(s.lam, r, s.info, 1e-7, n, s.Zc);
   if (evecs) {
-    int wpb = int(std::min<int64_t>(8, std::max<int64_t>(1, (200 * 1024) / (int64_t(n) * 8))));
-    const size_t smem = size_t(wpb) * n * sizeof(double);
+    int wpb = int(std::min<int64_t>(4, std::max<int64_t>(1, (200 * 1024) / (int64_t(n) * 16))));
+    const size_t smem = size_t(wpb) * 2 * n * sizeof(double);
     if ((e = cudaFuncSetAttribute(back_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(smem))) != cudaSuccess)
       return e;
-    back_transform_kernel<<<unsigned((r + wpb - 1) / wpb), wpb * 32, smem, st>>>(s.Vh, s.tau, n, r, s.Zc);
+    back_transform_kernel<<<unsigned((r + 2 * wpb - 1) / (2 * wpb)), wpb * 32, smem, st>>>(s.Vh, s.tau, n, r, s.Zc);
   }
   {
     dim3 b(32, 8), g(unsigned((r + 31) / 32), unsigned((n + 31) / 32));
