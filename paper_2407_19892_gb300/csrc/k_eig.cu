@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, 
       s = warp_sum(s);
       if (lane == 0 && more) Pn[it] = tn * s;
     }
-    // next step's reflector
+    // next step's reflector (after every warp of the CTA is done reading v, w)
+    __syncthreads();
     for (int i = threadIdx.x; i < m - 1; i += blockDim.x) v[i] = u[1 + i];
     tk = tn;
     if (!grid_barrier(bar, nb, status)) return;
