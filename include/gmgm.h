@@ -249,6 +249,32 @@ int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p,
                   const double* const* init, const gmgm_solve_opts* opts,
                   double* const* lambda_out, gmgm_solve_stats* stats);
 
+/* The same eigenvalue solve for callers that cannot allocate device memory
+ * at call time (a host whose own allocator has reserved the device, a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device
+ * synchronisation, a plugin with a fixed memory budget).  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ *   - No handle, no allocation: the solver's working vectors, status word
+ *     and statistics live in one fixed device array inside the library
+ *     (about 0.5 MB), which every device that loads the library holds until
+ *     the process exits.  The call makes no cudaMalloc/cudaFree.
+ *   - Runs on the calling thread's current device and on `cuda_stream`
+ *     (a cudaStream_t, NULL = legacy default stream).  The first call on a
+ *     device looks up the array's device address (a one-time, non-allocating
+ *     runtime query); make that first call before any stream capture.
+ *   - Limit: sum_l r_l <= 4096.  Larger problems, and every argument error
+ *     of gmgm_eigsolve, return GMGM_E_ARG before anything is enqueued.
+ *   - All calls share the one array and it keeps the last call's contents:
+ *     calls that may overlap on the GPU (different streams, or different
+ *     host threads) race and must be serialised by the caller.
+ *   - Arguments as gmgm_eigsolve.  `stats` (host, optional): if non-NULL the
+ *     call synchronises the stream, fills it and returns its status.
+ *     Otherwise device-detected problems are only visible in the returned
+ *     lambda values (the status word is private to this entry point). */
+int gmgm_eigsolve_static(const gmgm_problem* p, const double* const* init,
+                         const gmgm_solve_opts* opts, double* const* lambda_out,
+                         gmgm_solve_stats* stats, void* cuda_stream);
+
 /* ---- step 4: recomposition + per-row top-k ------------------------------ */
 
 typedef struct {

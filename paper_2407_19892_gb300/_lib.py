@@ -76,6 +76,9 @@ SIGNATURES = {
     "gmgm_eigsolve": (c_int, [c_vp, ctypes.POINTER(Problem), ctypes.POINTER(c_vp),
                               ctypes.POINTER(SolveOpts), ctypes.POINTER(c_vp),
                               ctypes.POINTER(SolveStats)]),
+    "gmgm_eigsolve_static": (c_int, [ctypes.POINTER(Problem), ctypes.POINTER(c_vp),
+                                     ctypes.POINTER(SolveOpts), ctypes.POINTER(c_vp),
+                                     ctypes.POINTER(SolveStats), c_vp]),
     "gmgm_topk_network": (c_int, [c_vp, c_i64, c_i32, c_vp, c_int, c_i64, c_vp, c_i32, c_int,
                                   c_vp, c_vp, ctypes.POINTER(TopkStats)]),
 }

@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <mutex>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -574,3 +575,171 @@ cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* co
 }
 
 }  // namespace gmgm
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the eigenvalue solve (gmgm_eigsolve_static).
+//
+// Some callers cannot allocate device memory when they call the library:
+// a host that has reserved the whole device for its own allocator, a
+// latency-critical loop that cannot afford cudaMalloc's implicit device
+// synchronisation, or a plugin whose memory budget is fixed up front.  For
+// them this entry point takes no handle and allocates nothing: its working
+// vectors, status word and statistics live in one file-scope device array of
+// fixed size, reserved when the library is loaded and held by every device
+// that loads it until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace gmgm {
+namespace {
+
+constexpr int kStaticMaxRank = 4096;  // sum of the ranks accepted
+constexpr size_t kStaticVecBytes =
+    size_t(kStaticMaxRank) * (13 * sizeof(double) + 2 * sizeof(float) + sizeof(int)) + 20 * 256;
+constexpr size_t kStaticBytes = kStaticVecBytes + 1024;  // + status word and stats
+
+}  // namespace
+
+// The scratch of gmgm_eigsolve_static.  In host code this name is only a
+// stand-in for the symbol; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_solve_static[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_addr[128] = {};  // per device: device address of g_solve_static
+
+// First call on a device: look up the array's device address (once).
+int static_scratch(int device, void** out) {
+  if (device < 0 || device >= 128) return GMGM_E_ARG;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[device]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_solve_static) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return GMGM_E_CUDA;
+    }
+    g_static_addr[device] = ptr;
+  }
+  *out = g_static_addr[device];
+  return GMGM_OK;
+}
+
+}  // namespace
+
+}  // namespace gmgm
+
+extern "C" int gmgm_eigsolve_static(const gmgm_problem* p, const double* const* init, const gmgm_solve_opts* o,
+                                    double* const* lambda_out, gmgm_solve_stats* stats, void* cuda_stream) {
+  using namespace gmgm;
+  if (!p || !lambda_out) return GMGM_E_ARG;
+  if (p->n_axes < 1 || p->n_axes > GMGM_MAX_AXES || p->n_modalities < 1 || p->n_modalities > GMGM_MAX_MODALITIES)
+    return GMGM_E_ARG;
+  int64_t total = 0;
+  for (int a = 0; a < p->n_axes; ++a) {
+    if (p->r[a] < 1 || !p->E[a] || !lambda_out[a] || (init && !init[a])) return GMGM_E_ARG;
+    total += p->r[a];
+  }
+  if (total > kStaticMaxRank) return GMGM_E_ARG;  // beyond the fixed scratch
+  int used[GMGM_MAX_AXES] = {0, 0, 0, 0};
+  for (int g = 0; g < p->n_modalities; ++g) {
+    const int k = p->mod_n_axes[g];
+    if (k < 1 || k > GMGM_MAX_AXES) return GMGM_E_ARG;
+    int seen = 0;
+    int64_t pts = 1;
+    for (int q = 0; q < k; ++q) {
+      const int a = p->mod_axes[g][q];
+      if (a < 0 || a >= p->n_axes || (seen & (1 << a))) return GMGM_E_ARG;
+      seen |= 1 << a;
+      used[a] = 1;
+      pts *= p->r[a];
+    }
+    if (pts > (int64_t(1) << 31)) return GMGM_E_ARG;
+  }
+  for (int a = 0; a < p->n_axes; ++a)
+    if (!used[a]) return GMGM_E_ARG;
+  gmgm_solve_opts opt = {1e-9, 200, 200, 1, 1};
+  if (o) {
+    opt = *o;
+    if (opt.tol <= 0) opt.tol = 1e-9;
+    if (opt.max_newton <= 0) opt.max_newton = 200;
+    if (opt.max_cg <= 0) opt.max_cg = 200;
+  }
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return GMGM_E_CUDA;
+  }
+  void* base = nullptr;
+  int rc = static_scratch(device, &base);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // layout of the array: vectors, then the status word, then the stats
+  char* b = static_cast<char*>(base);
+  int* d_status = reinterpret_cast<int*>(b + kStaticVecBytes);
+  gmgm_solve_stats* d_stats = reinterpret_cast<gmgm_solve_stats*>(b + kStaticVecBytes + 256);
+  Params P{};
+  P.L = p->n_axes;
+  P.off[0] = 0;
+  for (int a = 0; a < P.L; ++a) {
+    P.r[a] = p->r[a];
+    P.off[a + 1] = P.off[a] + p->r[a];
+    P.eps[a] = p->eps[a];
+    P.E[a] = p->E[a];
+    P.init[a] = init ? init[a] : nullptr;
+    P.out[a] = lambda_out[a];
+  }
+  P.N = P.off[P.L];
+  P.nmod = p->n_modalities;
+  for (int g = 0; g < P.nmod; ++g) {
+    P.mk[g] = p->mod_n_axes[g];
+    for (int q = 0; q < P.mk[g]; ++q) P.ma[g][q] = p->mod_axes[g][q];
+  }
+  P.tol = opt.tol;
+  P.max_newton = opt.max_newton;
+  P.max_cg = opt.max_cg;
+  P.fp32_phase = opt.fp32_phase;
+  P.gauge = opt.gauge;
+  P.has_init = init != nullptr;
+  Carve c(base);
+  const int N = P.N;
+  Vecs V;
+  V.E = c.take<double>(N);
+  V.x = c.take<double>(N);
+  V.g = c.take<double>(N);
+  V.lo = c.take<double>(N);
+  V.hd = c.take<double>(N);
+  V.d = c.take<double>(N);
+  V.rr = c.take<double>(N);
+  V.z = c.take<double>(N);
+  V.p = c.take<double>(N);
+  V.hp = c.take<double>(N);
+  V.dx = c.take<double>(N);
+  V.s1 = c.take<double>(N);
+  V.s2 = c.take<double>(N);
+  V.x32 = c.take<float>(N);
+  V.v32 = c.take<float>(N);
+  V.act = c.take<int>(N);
+  // the array keeps the previous call's contents: the status word starts at zero
+  if (cudaMemsetAsync(d_status, 0, sizeof(int), st) != cudaSuccess) {
+    cudaGetLastError();
+    return GMGM_E_CUDA;
+  }
+  const size_t smem = size_t(2) * kMaxLoop * sizeof(double);
+  if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
+    cudaGetLastError();
+    return GMGM_E_CUDA;
+  }
+  solve_kernel<<<1, kThreads, smem, st>>>(P, V, d_status, d_stats);
+  if (cudaGetLastError() != cudaSuccess) return GMGM_E_CUDA;
+  note_launch(1);
+  if (stats) {
+    if (cudaMemcpyAsync(stats, d_stats, sizeof(gmgm_solve_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return GMGM_E_CUDA;
+    }
+    return stats->status;
+  }
+  return GMGM_OK;
+}
+
