@@ -41,8 +41,10 @@ def parse():
     ap.add_argument("--r-cells", type=int, default=50)
     ap.add_argument("--k-cells", type=int, default=10)
     ap.add_argument("--k-genes", type=int, default=20)
-    ap.add_argument("--gram-prec", default="fp32", choices=["fp32", "bf16x3"])
-    ap.add_argument("--topk-prec", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--gram-prec", default="bf16x3", choices=["fp32", "bf16x3"])
+    ap.add_argument("--topk-prec", default="bf16", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="skip the one-step run of the plain FP32 form reported in detail")
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--seed", type=int, default=20240730)
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -355,6 +357,25 @@ def main():
                "d2h_bytes_per_step": (idx_h.numel() + val_h.numel() + gidx_h.numel() + gval_h.numel()) * 4}
         del host, dev_in
 
+    # ---- the plain FP32 form (SIMT Gram and screen), one step, for comparison ----
+    fp32_form = None
+    if not a.no_fp32_form and (gram_prec != g.FP32 or topk_prec != g.FP32):
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        q0.record(stream)
+        x32, _, _, _ = g.preprocess(counts, split=False, h=h)
+        r32 = g.fit_two_axis(x32, a.r_cells, a.genes, a.k_cells, a.k_genes, gram_prec=g.FP32, topk_prec=g.FP32,
+                             tol=a.tol, h=h)
+        q1.record(stream)
+        barrier()
+        ms32 = q0.elapsed_time(q1)
+        s32 = r32.topk_rows_stats["screen_ms"]
+        fp32_form = {"ms_per_step": ms32, "value": a.cells / (ms32 / 1e3), "screen_ms": s32,
+                     "screen_tflops": 2.0 * a.cells * a.cells * a.r_cells / (s32 / 1e3) / 1e12,
+                     "speedup_of_this_form": ms32 / ms}
+        del x32, r32
+
     # ---- roofline of the dominant kernel (the cell-axis top-k screen) ----
     pk, pk_kind = peaks()
     flops = 2.0 * a.cells * a.cells * a.r_cells
@@ -398,7 +419,8 @@ def main():
                    "l2": "inputs larger than L2 (8 GB counts per step)", "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clocks,
-        "detail": {"stage_ms": stage_ms, "solve": solve, "rows_uncertified": unc, "screen_ms": scr_ms,
+        "detail": {"stage_ms": stage_ms, "fp32_form": fp32_form, "solve": solve, "rows_uncertified": unc,
+                   "screen_ms": scr_ms,
                    "gene_topk": res.topk_cols_stats},
     }
     print(json.dumps(line), flush=True)
