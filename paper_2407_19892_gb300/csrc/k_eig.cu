@@ -3,7 +3,7 @@
 //   1. Householder tridiagonalisation Q^T S Q = T, one cooperative kernel with
 //      one bounded grid barrier per reflector (matrix in L2, FP64 bound);
 //   2. multisection with division-free Sturm counts for the wanted
-//      eigenvalues of T (eight lanes per eigenvalue);
+//      eigenvalues of T (sixteen lanes per eigenvalue);
 //   3. inverse iteration on T - lambda I (tridiagonal LU with partial
 //      pivoting, one thread per eigenvalue), then modified Gram-Schmidt inside
 //      clusters of nearly equal eigenvalues;
@@ -22,7 +22,8 @@ namespace gmgm {
 namespace {
 
 constexpr int kTriThreads = 256;
-constexpr int kSeg = 128;  // columns per update segment
+constexpr int kBatch = 8;     // independent row loads per lane in flight
+constexpr int kInvIters = 2;  // inverse-iteration solves (bisection eigenvalues are accurate to ~eps)
 
 __global__ void copy_sym_kernel(const double* __restrict__ S, int64_t lds, int n, double* __restrict__ A) {
   const int64_t i = int64_t(blockIdx.y) * blockDim.y + threadIdx.y;
@@ -89,7 +90,14 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, 
     for (int i = gwarp; i < m; i += total_warps) {
       const double* row = A + int64_t(1 + i) * n + 1;
       double s = 0.0;
-      for (int j = lane; j < m; j += 32) s += __ldcg(row + j) * v[j];
+      for (int j0 = lane; j0 < m; j0 += 32 * kBatch) {
+        double a[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) a[q] = j0 + 32 * q < m ? __ldcg(row + j0 + 32 * q) : 0.0;
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q)
+          if (j0 + 32 * q < m) s += a[q] * v[j0 + 32 * q];
+      }
       s = warp_sum(s);
       if (lane == 0) P[i] = tk * s;
     }
@@ -129,18 +137,30 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, 
     if (more && blockIdx.x == 0)
       for (int i = threadIdx.x; i < m - 1; i += blockDim.x) Vh[int64_t(k + 1) * n + k + 2 + i] = u[1 + i];
     // fused pass: rows i, cols j in k+2..n-1 (local index t = i - (k+1) >= 1)
-    const int segs = (m - 1 + kSeg - 1) / kSeg;
     for (int it = gwarp; it < (m - 1); it += total_warps) {
       const int t = 1 + it;
       double* row = A + int64_t(k + 1 + t) * n + k + 2;
       const double vi = v[t], wi = w[t];
       double s = 0.0;
-      for (int sg = 0; sg < segs; ++sg) {
-        const int j1 = min(m - 1, (sg + 1) * kSeg);
-        for (int jj = sg * kSeg + lane; jj < j1; jj += 32) {
-          const double a = tk != 0.0 ? __ldcg(row + jj) - (vi * w[1 + jj] + wi * v[1 + jj]) : __ldcg(row + jj);
-          if (tk != 0.0) row[jj] = a;
-          s += a * u[1 + jj];
+      const int mm = m - 1;
+      // kBatch independent L2 loads in flight per lane before any store
+      for (int j0 = lane; j0 < mm; j0 += 32 * kBatch) {
+        double a[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+          const int jj = j0 + 32 * q;
+          a[q] = jj < mm ? __ldcg(row + jj) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) {
+          const int jj = j0 + 32 * q;
+          if (jj < mm) {
+            if (tk != 0.0) {
+              a[q] -= vi * w[1 + jj] + wi * v[1 + jj];
+              row[jj] = a[q];
+            }
+            s += a[q] * u[1 + jj];
+          }
         }
       }
       s = warp_sum(s);
@@ -217,7 +237,7 @@ __device__ __forceinline__ int sturm_count(const double* dv, const double* e2, i
   return cnt;
 }
 
-constexpr int kMS = 8;  // lanes per eigenvalue (9-way multisection)
+constexpr int kMS = 16;  // lanes per eigenvalue (17-way multisection)
 
 // Lanes in groups of kMS find the ascending eigenvalues j0 + group: each
 // round evaluates kMS interior points of the current interval and keeps the
@@ -280,7 +300,7 @@ __global__ void inverse_iter_kernel(const double* __restrict__ dv, const double*
   const double nrm = fmax(info[3], DBL_MIN);
   const double tiny = DBL_EPSILON * nrm;
   for (int i = 0; i < n; ++i) Z[int64_t(i) * B + t] = hash_unit(uint32_t(seed_base + t), uint32_t(i));
-  for (int iter = 0; iter < 3; ++iter) {
+  for (int iter = 0; iter < kInvIters; ++iter) {
     // factor with partial pivoting while applying L^-1 to the right-hand side
     double a = dv[0] - lm, b = n > 1 ? ev[0] : 0.0;
     double y = Z[t];  // current y_i (after elimination of previous rows)
@@ -328,7 +348,7 @@ __global__ void inverse_iter_kernel(const double* __restrict__ dv, const double*
     }
     // scale (keeps the next solve in range) and, on the last pass, normalise
     double s = 1.0 / fmax(zmax, DBL_MIN);
-    if (iter == 2) {
+    if (iter == kInvIters - 1) {
       double nn = 0.0;
       for (int i = 0; i < n; ++i) {
         const double zi = Z[int64_t(i) * B + t] * s;
@@ -412,6 +432,7 @@ __global__ void back_transform_kernel(const double* __restrict__ Vh, const doubl
     if (tk == 0.0) continue;
     const double* vk = Vh + int64_t(k) * n;
     double y0 = 0.0, y1 = 0.0;
+#pragma unroll 4
     for (int i = k + 1 + lane; i < n; i += 32) {
       const double vv = __ldg(vk + i);
       y0 += vv * z0[i];
@@ -424,6 +445,7 @@ __global__ void back_transform_kernel(const double* __restrict__ Vh, const doubl
     }
     y0 *= tk;
     y1 *= tk;
+#pragma unroll 4
     for (int i = k + 1 + lane; i < n; i += 32) {
       const double vv = __ldg(vk + i);
       z0[i] -= y0 * vv;
@@ -456,7 +478,7 @@ __global__ void output_kernel(const double* __restrict__ lam, const double* __re
   }
 }
 
-constexpr int kInvBatch = 1024;
+constexpr int kInvBatch = 4096;
 
 struct EigScratch {
   double *A, *Vh, *tau, *dv, *ev, *e2, *P, *info, *lam, *u0, *u1, *u2, *Z, *Zc;
@@ -544,7 +566,7 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
   const int B = std::min(r, kInvBatch);
   for (int t0 = 0; t0 < r; t0 += B) {
     const int cnt = std::min(B, r - t0);
-    inverse_iter_kernel<<<unsigned((cnt + 63) / 64), 64, 0, st>>>(s.dv, s.ev, n, s.lam + t0, cnt, B, s.info,
+    inverse_iter_kernel<<<unsigned((cnt + 31) / 32), 32, 0, st>>>(s.dv, s.ev, n, s.lam + t0, cnt, B, s.info,
                                                                    s.u0, s.u1, s.u2, s.Z, t0);
     dim3 tb(32, 8), tg(unsigned((cnt + 31) / 32), unsigned((n + 31) / 32));
     transpose_kernel<<<tg, tb, 0, st>>>(s.Z, n, cnt, B, s.Zc, t0);
