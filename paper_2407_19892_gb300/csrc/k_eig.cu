@@ -3,7 +3,7 @@
 //   1. Householder tridiagonalisation Q^T S Q = T, one cooperative kernel with
 //      one bounded grid barrier per reflector (matrix in L2, FP64 bound);
 //   2. multisection with division-free Sturm counts for the wanted
-//      eigenvalues of T (sixteen lanes per eigenvalue);
+//      eigenvalues of T (eight lanes per eigenvalue);
 //   3. inverse iteration on T - lambda I (tridiagonal LU with partial
 //      pivoting, one thread per eigenvalue), then modified Gram-Schmidt inside
 //      clusters of nearly equal eigenvalues;
@@ -237,7 +237,7 @@ __device__ __forceinline__ int sturm_count(const double* dv, const double* e2, i
   return cnt;
 }
 
-constexpr int kMS = 16;  // lanes per eigenvalue (17-way multisection)
+constexpr int kMS = 8;  // lanes per eigenvalue (9-way multisection)
 
 // Lanes in groups of kMS find the ascending eigenvalues j0 + group: each
 // round evaluates kMS interior points of the current interval and keeps the
@@ -432,7 +432,6 @@ __global__ void back_transform_kernel(const double* __restrict__ Vh, const doubl
     if (tk == 0.0) continue;
     const double* vk = Vh + int64_t(k) * n;
     double y0 = 0.0, y1 = 0.0;
-#pragma unroll 4
     for (int i = k + 1 + lane; i < n; i += 32) {
       const double vv = __ldg(vk + i);
       y0 += vv * z0[i];
@@ -445,7 +444,6 @@ __global__ void back_transform_kernel(const double* __restrict__ Vh, const doubl
     }
     y0 *= tk;
     y1 *= tk;
-#pragma unroll 4
     for (int i = k + 1 + lane; i < n; i += 32) {
       const double vv = __ldg(vk + i);
       z0[i] -= y0 * vv;
