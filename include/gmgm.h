@@ -275,6 +275,68 @@ int gmgm_eigsolve_static(const gmgm_problem* p, const double* const* init,
                          const gmgm_solve_opts* opts, double* const* lambda_out,
                          gmgm_solve_stats* stats, void* cuda_stream);
 
+/* ---- learned warm start of the eigenvalue solve ------------------------- */
+/* Not part of the paper: Algorithm 1 starts the solve at Lam^0 = 1/E.  A
+ * small network predicts the start instead; the solve then runs to the same
+ * tolerance, so the prediction changes the iteration count, never the result
+ * (and a non-finite prediction falls back to 1/E).  Two-axis problems only.
+ *
+ * Features (132 FP32): for each axis, the interpolated log E at 64 evenly
+ * spaced rank positions minus log(mean E); then log(r_0)/8, log(r_1)/8,
+ * log tr E_0 - log tr E_1, log E_0[0] - log E_1[0].
+ * Targets (128 FP32): for each axis, the interpolated log(lam_i E_i) at the
+ * same 64 positions.
+ * Network: 132 -> 256 -> 256 -> 128, ReLU hidden layers, linear output, MSE.
+ * Parameters: one FP32 vector of GMGM_MLP_PARAMS values, in order
+ * W1 [256][132], b1 [256], W2 [256][256], b2 [256], W3 [128][256], b3 [128]. */
+#define GMGM_MLP_IN 132
+#define GMGM_MLP_HIDDEN 256
+#define GMGM_MLP_OUT 128
+#define GMGM_MLP_PARAMS (256 * 132 + 256 + 256 * 256 + 256 + 128 * 256 + 128)
+
+typedef struct {
+  int32_t steps;   /* Adam steps */
+  int32_t batch;   /* mini-batch size (capped at n) */
+  float lr, beta1, beta2, eps;
+  uint64_t seed;   /* mini-batch order (seeded shuffles on the host) */
+} gmgm_train_opts;
+
+/* Features of a two-axis problem (E_0: r_0, E_1: r_1, device FP64,
+ * descending, > 0) into `feats` (device, 132 FP32). */
+int gmgm_warmstart_features(gmgm_handle* h, const double* E0, int32_t r0,
+                            const double* E1, int32_t r1, float* feats);
+
+/* Targets of a solved problem (lam_0, lam_1 device FP64) into `targets`
+ * (device, 128 FP32). */
+int gmgm_warmstart_targets(gmgm_handle* h, const double* E0, int32_t r0,
+                           const double* E1, int32_t r1, const double* lam0,
+                           const double* lam1, float* targets);
+
+/* Network output for n feature rows (device n x 132) into `out` (device
+ * n x 128). */
+int gmgm_mlp_forward(gmgm_handle* h, const float* params, const float* feats,
+                     int32_t n, float* out);
+
+/* MSE loss of n rows and its gradient w.r.t. the parameters (device,
+ * GMGM_MLP_PARAMS floats; may be NULL).  `loss` (host, optional): if given the
+ * call synchronises and stores the loss. */
+int gmgm_mlp_loss_grad(gmgm_handle* h, const float* params, const float* feats,
+                       const float* targets, int32_t n, float* grad, float* loss);
+
+/* Train in place with Adam: `params` (device, in/out), `adam_state` (device,
+ * 2 * GMGM_MLP_PARAMS floats, zero for a fresh start), n rows of features and
+ * targets (device).  `final_loss` (host, optional): loss of the last
+ * mini-batch (synchronises). */
+int gmgm_warmstart_train(gmgm_handle* h, float* params, float* adam_state,
+                         const float* feats, const float* targets, int32_t n,
+                         const gmgm_train_opts* opts, float* final_loss);
+
+/* Predicted start lam_0 (r_0), lam_1 (r_1) (device FP64) for the solve's
+ * `init`: lam_i = exp(interpolated prediction) / E_i, at least `eps`. */
+int gmgm_warmstart_infer(gmgm_handle* h, const float* params, const double* E0,
+                         int32_t r0, const double* E1, int32_t r1, double eps,
+                         double* lam0_out, double* lam1_out);
+
 /* ---- step 4: recomposition + per-row top-k ------------------------------ */
 
 typedef struct {

@@ -51,6 +51,15 @@ class SolveStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("steps", c_i32), ("batch", c_i32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+MLP_IN, MLP_HIDDEN, MLP_OUT = 132, 256, 128
+MLP_PARAMS = 256 * 132 + 256 + 256 * 256 + 256 + 128 * 256 + 128
+
+
 class TopkStats(ctypes.Structure):
     _fields_ = [("rows_uncertified", c_i64), ("rows_exact", c_i64), ("candidates", c_i64),
                 ("screen_ms", c_dbl), ("rescore_ms", c_dbl), ("screen_err_ratio", c_dbl)]
@@ -79,6 +88,13 @@ SIGNATURES = {
     "gmgm_eigsolve_static": (c_int, [ctypes.POINTER(Problem), ctypes.POINTER(c_vp),
                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(c_vp),
                                      ctypes.POINTER(SolveStats), c_vp]),
+    "gmgm_warmstart_features": (c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp]),
+    "gmgm_warmstart_targets": (c_int, [c_vp, c_vp, c_i32, c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "gmgm_mlp_forward": (c_int, [c_vp, c_vp, c_vp, c_i32, c_vp]),
+    "gmgm_mlp_loss_grad": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i32, c_vp, ctypes.POINTER(ctypes.c_float)]),
+    "gmgm_warmstart_train": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(TrainOpts),
+                                     ctypes.POINTER(ctypes.c_float)]),
+    "gmgm_warmstart_infer": (c_int, [c_vp, c_vp, c_vp, c_i32, c_vp, c_i32, c_dbl, c_vp, c_vp]),
     "gmgm_topk_network": (c_int, [c_vp, c_i64, c_i32, c_vp, c_int, c_i64, c_vp, c_i32, c_int,
                                   c_vp, c_vp, ctypes.POINTER(TopkStats)]),
 }

@@ -250,6 +250,100 @@ int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p, const double* const* in
   return GMGM_OK;
 }
 
+// ---- learned warm start ----------------------------------------------------
+
+static int ws_check_axes(gmgm_handle* h, const double* E0, int32_t r0, const double* E1, int32_t r1,
+                         const char* who) {
+  if (!E0 || !E1 || r0 < 2 || r1 < 2)
+    return fail(h, GMGM_E_ARG, std::string(who) + ": need two axes with ranks >= 2");
+  return GMGM_OK;
+}
+
+int gmgm_warmstart_features(gmgm_handle* h, const double* E0, int32_t r0, const double* E1, int32_t r1,
+                            float* feats) {
+  if (!h) return GMGM_E_ARG;
+  int rc = ws_check_axes(h, E0, r0, E1, r1, "gmgm_warmstart_features");
+  if (rc) return rc;
+  if (!feats) return fail(h, GMGM_E_ARG, "gmgm_warmstart_features: null output");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  GMGM_CUDA_TRY(h, gmgm::launch_features(h, E0, r0, E1, r1, feats));
+  return GMGM_OK;
+}
+
+int gmgm_warmstart_targets(gmgm_handle* h, const double* E0, int32_t r0, const double* E1, int32_t r1,
+                           const double* lam0, const double* lam1, float* targets) {
+  if (!h) return GMGM_E_ARG;
+  int rc = ws_check_axes(h, E0, r0, E1, r1, "gmgm_warmstart_targets");
+  if (rc) return rc;
+  if (!lam0 || !lam1 || !targets) return fail(h, GMGM_E_ARG, "gmgm_warmstart_targets: null argument");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  GMGM_CUDA_TRY(h, gmgm::launch_targets(h, E0, r0, E1, r1, lam0, lam1, targets));
+  return GMGM_OK;
+}
+
+int gmgm_mlp_forward(gmgm_handle* h, const float* params, const float* feats, int32_t n, float* out) {
+  if (!h) return GMGM_E_ARG;
+  if (!params || !feats || !out || n < 1 || n > (1 << 20))
+    return fail(h, GMGM_E_ARG, "gmgm_mlp_forward: need buffers and 1 <= n <= 2^20");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, gmgm::mlp_scratch_bytes(n, 0));
+  if (rc) return rc;
+  GMGM_CUDA_TRY(h, gmgm::mlp_forward(h, params, feats, n, out, h->scratch));
+  return GMGM_OK;
+}
+
+int gmgm_mlp_loss_grad(gmgm_handle* h, const float* params, const float* feats, const float* targets, int32_t n,
+                       float* grad, float* loss) {
+  if (!h) return GMGM_E_ARG;
+  if (!params || !feats || !targets || n < 1 || n > (1 << 20))
+    return fail(h, GMGM_E_ARG, "gmgm_mlp_loss_grad: need buffers and 1 <= n <= 2^20");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  const size_t need = gmgm::mlp_scratch_bytes(n, 0);
+  int rc = gmgm::ensure_scratch(h, need + 512);
+  if (rc) return rc;
+  float* loss_dev = reinterpret_cast<float*>(static_cast<char*>(h->scratch) + gmgm::Carve::round(need));
+  GMGM_CUDA_TRY(h, gmgm::mlp_loss_grad(h, params, feats, targets, n, grad, loss_dev, h->scratch));
+  if (loss) {
+    GMGM_CUDA_TRY(h, cudaMemcpyAsync(loss, loss_dev, 4, cudaMemcpyDeviceToHost, h->stream));
+    GMGM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return GMGM_OK;
+}
+
+int gmgm_warmstart_train(gmgm_handle* h, float* params, float* adam_state, const float* feats, const float* targets,
+                         int32_t n, const gmgm_train_opts* opts, float* final_loss) {
+  if (!h) return GMGM_E_ARG;
+  if (!params || !adam_state || !feats || !targets || !opts || n < 1 || n > (1 << 20) || opts->steps < 0 ||
+      opts->steps > (1 << 24) || opts->batch < 1 || !(opts->lr > 0.f))
+    return fail(h, GMGM_E_ARG, "gmgm_warmstart_train: bad buffers or options");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  const int B = opts->batch < n ? opts->batch : n;
+  const size_t need = gmgm::mlp_scratch_bytes(B, opts->steps);
+  int rc = gmgm::ensure_scratch(h, need + 512);
+  if (rc) return rc;
+  float* loss_dev = reinterpret_cast<float*>(static_cast<char*>(h->scratch) + gmgm::Carve::round(need));
+  GMGM_CUDA_TRY(h, gmgm::mlp_train(h, params, adam_state, feats, targets, n, opts, loss_dev, h->scratch));
+  if (final_loss) {
+    GMGM_CUDA_TRY(h, cudaMemcpyAsync(final_loss, loss_dev, 4, cudaMemcpyDeviceToHost, h->stream));
+    GMGM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return GMGM_OK;
+}
+
+int gmgm_warmstart_infer(gmgm_handle* h, const float* params, const double* E0, int32_t r0, const double* E1,
+                         int32_t r1, double eps, double* lam0_out, double* lam1_out) {
+  if (!h) return GMGM_E_ARG;
+  int rc = ws_check_axes(h, E0, r0, E1, r1, "gmgm_warmstart_infer");
+  if (rc) return rc;
+  if (!params || !lam0_out || !lam1_out) return fail(h, GMGM_E_ARG, "gmgm_warmstart_infer: null argument");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  rc = gmgm::ensure_scratch(h, gmgm::mlp_scratch_bytes(1, 0));
+  if (rc) return rc;
+  GMGM_CUDA_TRY(h, gmgm::warmstart_infer(h, params, E0, r0, E1, r1, eps > 0 ? eps : 0.0, lam0_out, lam1_out,
+                                         h->scratch));
+  return GMGM_OK;
+}
+
 int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64,
                       int64_t ldv, const double* psi, int32_t k, gmgm_prec prec,
                       int32_t* idx_out, float* val_out, gmgm_topk_stats* stats) {

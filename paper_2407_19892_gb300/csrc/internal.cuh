@@ -87,6 +87,18 @@ cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* co
                          const gmgm_solve_opts* o, double* const* out, void* scratch,
                          gmgm_solve_stats* d_stats);
 
+size_t mlp_scratch_bytes(int batch, int64_t steps);
+cudaError_t launch_features(gmgm_handle* h, const double* E0, int r0, const double* E1, int r1, float* out);
+cudaError_t launch_targets(gmgm_handle* h, const double* E0, int r0, const double* E1, int r1, const double* l0,
+                           const double* l1, float* out);
+cudaError_t mlp_forward(gmgm_handle* h, const float* P, const float* X, int B, float* out, void* scratch);
+cudaError_t mlp_loss_grad(gmgm_handle* h, const float* P, const float* X, const float* T, int B, float* G,
+                          float* loss_dev, void* scratch);
+cudaError_t mlp_train(gmgm_handle* h, float* P, float* adam, const float* X, const float* T, int n,
+                      const gmgm_train_opts* o, float* loss_dev, void* scratch);
+cudaError_t warmstart_infer(gmgm_handle* h, const float* P, const double* E0, int r0, const double* E1, int r1,
+                            double eps, double* l0, double* l1, void* scratch);
+
 size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec);
 int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
              const double* psi, int32_t k, gmgm_prec prec, int32_t* idx, float* val,
