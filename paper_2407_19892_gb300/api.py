@@ -257,16 +257,23 @@ class TwoAxisResult:
 
 def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols: int,
                  gram_prec: int = L.FP32, topk_prec: int = L.FP32, xt_hi=None, xt_lo=None, ld_t=0,
-                 tol: float = 1e-9, fp32_phase=True, init=None, h: Handle = None) -> TwoAxisResult:
+                 tol: float = 1e-9, fp32_phase=True, init=None, warm_params=None,
+                 h: Handle = None) -> TwoAxisResult:
     """Algorithm 1 on a centred matrix X (rows x cols, FP32, on the GPU):
     S_cols = X^T X, its eigenpairs (FP64), the row-axis vectors by the dual
-    lift, the eigenvalue solve, and both per-row top-k networks."""
+    lift, the eigenvalue solve (from `init`, or from the learned start when
+    `warm_params` is given, else from 1/E), and both per-row top-k networks."""
     h = h or handle(x.device)
     S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, h=h)
     rmax = max(r_rows, r_cols)
     ev, W = spectra(S, rmax, True, h=h)
     e_cols, v_cols = ev[:r_cols].contiguous(), W[:, :r_cols].contiguous()
     e_rows = ev[:r_rows].contiguous()
+    if init is None and warm_params is not None:
+        i0, i1 = torch.empty_like(e_rows), torch.empty_like(e_cols)
+        h.check(h.lib.gmgm_warmstart_infer(h.h, _ptr(warm_params), _ptr(e_rows), r_rows, _ptr(e_cols), r_cols,
+                                           0.0, _ptr(i0), _ptr(i1)))
+        init = [i0, i1]
     v_rows = lift(x, W[:, :r_rows].contiguous(), e_rows, r_rows, h=h)
     (lam_rows, lam_cols), st = eigsolve([e_rows, e_cols], [(0, 1)], tol=tol, fp32_phase=fp32_phase,
                                         init=init, h=h)

@@ -88,13 +88,14 @@ def infer(params, E0, E1, eps=0.0, h=None):
     return l0, l1
 
 
-def method_problem(seed, device, cells=None, genes=None, r_cells=None):
+def method_problem(seed, device, cells=None, genes=None, r_cells=None, cell_range=(1000, 20000),
+                   gene_range=(100, 600)):
     """One synthetic scRNA-like problem through the method's first steps on
     the GPU: returns (E_cells, E_genes) for the eigenvalue solve."""
     from synth import scrna_counts
     rng = np.random.default_rng(seed)
-    cells = cells or int(np.exp(rng.uniform(np.log(1000), np.log(20000))))
-    genes = genes or int(np.exp(rng.uniform(np.log(100), np.log(600))))
+    cells = cells or int(np.exp(rng.uniform(np.log(cell_range[0]), np.log(cell_range[1]))))
+    genes = genes or int(np.exp(rng.uniform(np.log(gene_range[0]), np.log(gene_range[1]))))
     r_cells = r_cells or int(rng.integers(8, min(100, genes // 2)))
     clusters = int(rng.integers(4, 40))
     counts = scrna_counts(cells, genes, clusters, seed=int(seed), device=device)
@@ -104,12 +105,12 @@ def method_problem(seed, device, cells=None, genes=None, r_cells=None):
     return e[:r_cells].contiguous(), e.contiguous()
 
 
-def method_pairs(n, seed=0, device="cuda", tol=1e-9):
+def method_pairs(n, seed=0, device="cuda", tol=1e-9, **ranges):
     """n (features, targets) pairs: the method's own cold-start solutions of
     seeded synthetic problems."""
     F, T = [], []
     for i in range(n):
-        e0, e1 = method_problem(seed * 100003 + i, device)
+        e0, e1 = method_problem(seed * 100003 + i, device, **ranges)
         (l0, l1), st = eigsolve([e0, e1], [(0, 1)], tol=tol)
         if st["status"] != 0:
             continue
