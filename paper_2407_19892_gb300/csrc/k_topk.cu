@@ -167,8 +167,8 @@ __device__ __forceinline__ bool better(double a, int ja, double b, int jb) { ret
 __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv, const double* __restrict__ psi,
                                int k, const int* __restrict__ rows, int64_t m_host, const int* __restrict__ count_dev,
                                const int32_t* __restrict__ cidx, const float* __restrict__ cval,
-                               const float* __restrict__ thr, const unsigned* __restrict__ colmax_bits, double u,
-                               int32_t* __restrict__ idx_out, float* __restrict__ val_out,
+                               const float* __restrict__ thr, int thr_n, const unsigned* __restrict__ colmax_bits,
+                               double u, int32_t* __restrict__ idx_out, float* __restrict__ val_out,
                                int* __restrict__ flag_list, int* __restrict__ flag_count,
                                unsigned* __restrict__ err_bits) {
   const int lane = threadIdx.x & 31;
@@ -217,7 +217,10 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
       if (lane == 0 && ratio > 0.0) atomicMax(err_bits, __float_as_uint(float(fmin(ratio, 1e30))));
     }
     const double qk = __shfl_sync(0xffffffffu, key, k - 1);
-    const double t = double(thr[mi]);
+    // the best excluded screened value: the largest of the row's list minima
+    // (-1 for a list that saw every one of its columns)
+    double t = double(thr[mi * thr_n]);
+    for (int q = 1; q < thr_n; ++q) t = fmax(t, double(thr[mi * thr_n + q]));
     const bool certified = t < 0.0 || qk > t + bnd;
     if (lane < k) {
       idx_out[i * k + lane] = kj == INT_MAX ? -1 : kj;
@@ -366,12 +369,12 @@ double screen_unit(gmgm_prec prec, int r) {
 
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
                     const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
-                    const float* thr, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
+                    const float* thr, int thr_n, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
                     int* flag_list, int* flag_count, unsigned* err_bits) {
   // one warp per row; the grid covers at most d rows (grid-stride beyond)
   const unsigned blocks = unsigned(std::min<int64_t>((d * 32 + 255) / 256, 65536));
-  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, cval, thr, colmax_bits,
-                                        u, idx, val, flag_list, flag_count, err_bits);
+  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, cval, thr, thr_n,
+                                        colmax_bits, u, idx, val, flag_list, flag_count, err_bits);
 }
 
 // Exact FP64 top-k of the listed rows, column-parallel: a row's columns are
@@ -406,7 +409,7 @@ size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
   b += Carve::round(size_t(d) * rpad * 4) * 2;  // A, B
   b += Carve::round(size_t(r + 1) * 4);         // colmax + max row norm
   b += Carve::round(size_t(d) * kC * 4) * 2;    // level-1 candidates
-  b += Carve::round(size_t(d) * 4);             // level-1 thr
+  b += Carve::round(size_t(d) * 8);             // thresholds (up to two per row)
   b += Carve::round(size_t(d) * 4);             // flag list
   b += Carve::round(size_t(kExactCap) * 12) + 256;  // exact partial lists
   b += Carve::round(64);                        // counters
@@ -424,7 +427,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   unsigned* colmax = c.take<unsigned>(r + 1);  // [r] = max row norm
   int32_t* cidx = c.take<int32_t>(size_t(d) * kC);
   float* cval = c.take<float>(size_t(d) * kC);
-  float* thr = c.take<float>(d);
+  float* thr = c.take<float>(2 * d);  // per row: one threshold (FP32 screen) or two (tensor-core screen)
   int* flag1 = c.take<int>(d);
   double* part_v = c.take<double>(kExactCap);
   int* part_j = c.take<int>(kExactCap);
@@ -452,7 +455,8 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     GMGM_CUDA_TRY(h, launch_screen_tc(h, d, r, V, v_fp64, ldv, psi, prec, cidx, cval, thr, tc_scratch));
   }
   if (st) cudaEventRecord(ev[1], s);
-  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, colmax, screen_unit(prec, r),
+  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, prec == GMGM_FP32 ? 1 : 2,
+                 colmax, screen_unit(prec, r),
                  idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
   note_launch(prec == GMGM_FP32 ? 4 : 3);
   // rows the screen could not certify: exact FP64 scan (the count is read

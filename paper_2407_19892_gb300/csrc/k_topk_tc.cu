@@ -2,20 +2,25 @@
 // (Algorithm 1: threshold simultaneously with recomposition), sm_103a.
 //
 // Persistent, warp-specialised kernel, one CTA per SM:
-//   warp 0      TMA producer: the CTA's A rows (bf16(V psi), 256 rows = two
-//               128-row MMA tiles) once per row block, then every B tile
-//               (bf16(V), 128 rows) into a 6-stage shared-memory ring;
-//   warp 1      MMA issuer (one thread): per B tile, two accumulators
-//               D_h[128 x 128] = A_h B^T (K = 64 in four K=16 steps), FP32 in
-//               TMEM, double-buffered (4 x 128 of the 512 TMEM columns);
-//   warps 2-9   epilogue: thread = one row; tcgen05.ld 32 columns at a time,
-//               the chunk's max |v| against the row's running kC-th best
-//               (one FMNMX per element), and only when it beats it an insert
-//               into the row's kC-slot candidate list (shared memory).
-// All CTAs sweep the B tiles in the same order, so a B tile read from HBM
-// by the first CTA is served from L2 to the others.  Every wait is bounded;
-// on timeout the kernel records GMGM_DEV_TIMEOUT and leaves after freeing
-// its TMEM.
+//   warp 0      TMA producer: the CTA's 128 A rows (bf16(V psi)) once per row
+//               block, then every B tile (bf16(V), 256 rows) into a 4-stage
+//               shared-memory ring;
+//   warp 1      MMA issuer (one thread): per B tile D[128 x 256] = A B^T
+//               (K = 64 in four K=16 steps), FP32 in TMEM, double-buffered
+//               (2 x 256 of the 512 TMEM columns);
+//   warps 2-9   epilogue: two threads per row (one per 128-column half of the
+//               tile), each with a 16-slot candidate list; tcgen05.ld 32
+//               columns at a time, one max per element against the pair's
+//               shared threshold, and only when it is beaten a per-lane insert
+//               (a bitmask of the winners, values pulled out of registers by a
+//               select tree).
+// The pair's threshold is the larger of the two lists' minima (each list
+// publishes its minimum in shared memory once full); a stale read only admits
+// more candidates.  Every column left out of a row's two lists has a screened
+// value <= the larger final minimum, which is the row's certification
+// threshold.  All CTAs sweep the B tiles in the same order (L2 reuse).  Every
+// wait is bounded; on timeout the kernel records GMGM_DEV_TIMEOUT and leaves
+// after freeing its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -30,16 +35,17 @@
 namespace gmgm {
 namespace {
 
-constexpr int kTM = 128;                    // rows per MMA tile
-constexpr int kHalves = 2;                  // MMA tiles per row block
-constexpr int kRB = kTM * kHalves;          // rows per row block
-constexpr int kTN = 128;                    // columns per B tile
-constexpr int kKP = 64;                     // padded K (bf16 elements, one 128-byte row)
-constexpr int kStages = 6;
+constexpr int kTM = 128;                     // rows per row block (MMA M)
+constexpr int kTN = 256;                     // columns per B tile (MMA N)
+constexpr int kKP = 64;                      // padded K (bf16 elements, one 128-byte row)
+constexpr int kStages = 4;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kTileBytes = kTM * kKP * 2;   // 16 KB, A tile and B tile alike
-constexpr long long kSpin = 1ll << 23;      // polls per bounded wait
+constexpr int kATile = kTM * kKP * 2;        // 16 KB
+constexpr int kBTile = kTN * kKP * 2;        // 32 KB
+constexpr int kCH = kC / 2;                  // slots per half-row list
+constexpr int kLists = 2 * kTM;              // (row, half) lists per CTA
+constexpr long long kSpin = 1ll << 23;       // polls per bounded wait
 
 struct __align__(8) Bars {
   uint64_t full[kStages];
@@ -53,8 +59,8 @@ struct __align__(8) Bars {
   int abort;
 };
 
-constexpr size_t kSmemBytes = 1024 /*align slack*/ + size_t(kHalves) * kTileBytes + size_t(kStages) * kTileBytes +
-                              size_t(2) * kC * kRB * 4 + sizeof(Bars);
+constexpr size_t kSmemBytes = 1024 /*align slack*/ + size_t(kATile) + size_t(kStages) * kBTile +
+                              size_t(2) * kCH * kLists * 4 + size_t(kLists) * 8 + sizeof(Bars);
 
 __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
   atomicExch(&bs->abort, 1);
@@ -63,14 +69,12 @@ __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
 
 __device__ __forceinline__ bool aborted(Bars* bs) { return *reinterpret_cast<volatile int*>(&bs->abort) != 0; }
 
-// Candidate list of one row, slot-major (stride kRB) so a warp's rows are
-// consecutive words.  Same policy as list_offer: fill, then replace the
-// minimum only by a strictly larger value.  Kept out of line (inserts are
-// rare); the state travels by value so it stays in registers.
+// One (row, half) candidate list, slot-major (stride kLists): fill, then
+// replace the minimum.  Out of line (inserts are rare); state by value.
 struct ListState {
   int cnt;
   int minpos;
-  float minv;
+  float minv;  // minimum once full, else -1
 };
 
 // r[e] for a per-lane runtime e without leaving registers: a 5-level select
@@ -88,20 +92,25 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&r)[32], int e) {
   return (e & 1) ? d[1] : d[0];
 }
 
-__device__ __noinline__ ListState offer_strided(float* lv, int* li, ListState st, float v, int j) {
-  if (st.cnt < kC) {
-    lv[st.cnt * kRB] = v;
-    li[st.cnt * kRB] = j;
+// The published minimum carries the row block it belongs to (high word), so
+// a partner still in the previous row block is never mistaken for this one.
+__device__ __noinline__ ListState offer16(float* lv, int* li, unsigned long long* pub, unsigned tag, ListState st,
+                                          float v, int j) {
+  if (st.cnt < kCH) {
+    lv[st.cnt * kLists] = v;
+    li[st.cnt * kLists] = j;
     ++st.cnt;
-    if (st.cnt < kC) return st;
+    if (st.cnt < kCH) return st;
   } else {
-    lv[st.minpos * kRB] = v;
-    li[st.minpos * kRB] = j;
+    lv[st.minpos * kLists] = v;
+    li[st.minpos * kLists] = j;
   }
   st.minv = lv[0];
   st.minpos = 0;
-  for (int c = 1; c < kC; ++c)
-    if (lv[c * kRB] < st.minv) st.minv = lv[c * kRB], st.minpos = c;
+  for (int c = 1; c < kCH; ++c)
+    if (lv[c * kLists] < st.minv) st.minv = lv[c * kLists], st.minpos = c;
+  *reinterpret_cast<volatile unsigned long long*>(pub) =
+      (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(st.minv);  // publish for the partner
   return st;
 }
 
@@ -112,10 +121,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sB = sA + kHalves * kTileBytes;
-  float* lv = reinterpret_cast<float*>(sB + kStages * kTileBytes);
-  int* li = reinterpret_cast<int*>(lv + kC * kRB);
-  Bars* bs = reinterpret_cast<Bars*>(li + kC * kRB);
+  uint8_t* sB = sA + kATile;
+  float* lv = reinterpret_cast<float*>(sB + kStages * kBTile);
+  int* li = reinterpret_cast<int*>(lv + kCH * kLists);
+  unsigned long long* pubs = reinterpret_cast<unsigned long long*>(li + kCH * kLists);  // [kLists] (tag, minimum)
+  Bars* bs = reinterpret_cast<Bars*>(pubs + kLists);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = bs->tmem_base;
-  const int nrb = (n + kRB - 1) / kRB;
+  const int nrb = (n + kTM - 1) / kTM;
   const int ntiles = (n + kTN - 1) / kTN;
 
   if (warp == 0) {
@@ -147,8 +157,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           raise_abort(bs, status);
           break;
         }
-        tc::mbar_arrive_expect_tx(&bs->afull, kHalves * kTileBytes);
-        for (int hh = 0; hh < kHalves; ++hh) tc::tma_load_2d(sA + hh * kTileBytes, &tmA, &bs->afull, 0, rb * kRB + hh * kTM);
+        tc::mbar_arrive_expect_tx(&bs->afull, kATile);
+        tc::tma_load_2d(sA, &tmA, &bs->afull, 0, rb * kTM);
         for (int t = 0; t < ntiles; ++t, ++issued) {
           const int s = int(issued % kStages);
           const uint32_t k = uint32_t(issued / kStages);
@@ -156,8 +166,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             raise_abort(bs, status);
             break;
           }
-          tc::mbar_arrive_expect_tx(&bs->full[s], kTileBytes);
-          tc::tma_load_2d(sB + s * kTileBytes, &tmB, &bs->full[s], 0, t * kTN);
+          tc::mbar_arrive_expect_tx(&bs->full[s], kBTile);
+          tc::tma_load_2d(sB + s * kBTile, &tmB, &bs->full[s], 0, t * kTN);
         }
         if (aborted(bs)) break;
       }
@@ -171,6 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
+      const uint32_t abase = tc::smem_u32(sA);
       long long used = 0, accu = 0;
       int rbi = 0;
       for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x, ++rbi) {
@@ -187,14 +198,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc::fence_after_sync();
-          const uint32_t bbase = tc::smem_u32(sB + s * kTileBytes);
-#pragma unroll
-          for (int hh = 0; hh < kHalves; ++hh) {
-            const uint32_t abase = tc::smem_u32(sA + hh * kTileBytes);
-            const uint32_t d = tmem + uint32_t((b * kHalves + hh) * kTN);
-            for (int ks = 0; ks < ksteps; ++ks)
-              tc::mma_bf16(d, tc::sdesc_k128(abase + ks * 32), tc::sdesc_k128(bbase + ks * 32), idesc, ks > 0);
-          }
+          const uint32_t bbase = tc::smem_u32(sB + s * kBTile);
+          const uint32_t d = tmem + uint32_t(b * kTN);
+          for (int ks = 0; ks < ksteps; ++ks)
+            tc::mma_bf16(d, tc::sdesc_k128(abase + ks * 32), tc::sdesc_k128(bbase + ks * 32), idesc, ks > 0);
           tc::mma_commit(&bs->empty[s]);
           tc::mma_commit(&bs->accf[b]);
         }
@@ -207,15 +214,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue ----------------
     const int ew = warp - 2;
-    const int half = ew >> 2;
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row_local = half * kTM + q * 32 + lane;
-    float* mlv = lv + row_local;
-    int* mli = li + row_local;
+    const int half = ew >> 2;  // 128-column half of the tile
+    const int q = warp & 3;    // TMEM lane quarter this warp may access
+    const int row_local = q * 32 + lane;
+    const int L = half * kTM + row_local;
+    float* mlv = lv + L;
+    int* mli = li + L;
+    unsigned long long* mine = pubs + L;
+    const volatile unsigned long long* partner = pubs + (1 - half) * kTM + row_local;
+    *reinterpret_cast<volatile unsigned long long*>(mine) = ~0ull;  // no row block yet
     long long accu = 0;
     for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x) {
-      const int i = rb * kRB + row_local;
+      const int i = rb * kTM + row_local;
+      const unsigned tag = unsigned(rb);
       ListState st{0, 0, -1.f};
+      auto partner_min = [&]() {
+        const unsigned long long pv = *partner;
+        return unsigned(pv >> 32) == tag ? __uint_as_float(unsigned(pv)) : -1.f;
+      };
       for (int t = 0; t < ntiles; ++t, ++accu) {
         const int b = int(accu & 1);
         if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin)) {
@@ -223,20 +239,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc::fence_after_sync();
-        const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t((b * kHalves + half) * kTN);
-        const int j0 = t * kTN;
-        // the whole 128-column row slice in one round trip, then hand the
+        const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * kTN + half * 128);
+        const int j0 = t * kTN + half * 128;
+        // the whole 128-column slice in one round trip, then hand the
         // accumulator back to the MMA warp before scanning
-        uint32_t r[kTN / 32][32];
+        uint32_t r[4][32];
         __syncwarp();
 #pragma unroll
-        for (int c = 0; c < kTN / 32; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
+        for (int c = 0; c < 4; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
         tc::tmem_ld_wait();
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
+        float thr = fmaxf(st.minv, partner_min());
 #pragma unroll
-        for (int c = 0; c < kTN / 32; ++c) {
+        for (int c = 0; c < 4; ++c) {
           float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // four short max chains
 #pragma unroll
           for (int e = 0; e < 32; e += 4) {
@@ -245,28 +262,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             m2 = fmaxf(m2, fabsf(__uint_as_float(r[c][e + 2])));
             m3 = fmaxf(m3, fabsf(__uint_as_float(r[c][e + 3])));
           }
-          if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > st.minv) {
-            // per lane: a bitmask of the columns above the threshold, then
-            // each set bit's value pulled out of registers by a select tree
+          if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr) {
             uint32_t mask = 0;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(r[c][e])) > st.minv ? 1u : 0u) << e;
+            for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(r[c][e])) > thr ? 1u : 0u) << e;
             while (mask) {
               const int e = __ffs(mask) - 1;
               mask &= mask - 1;
               const float v = fabsf(__uint_as_float(pick32(r[c], e)));
               const int j = j0 + c * 32 + e;
-              if (v > st.minv && j < n && j != i) st = offer_strided(mlv, mli, st, v, j);
+              if (v > thr && j < n && j != i) {
+                st = offer16(mlv, mli, mine, tag, st, v, j);
+                thr = fmaxf(st.minv, partner_min());
+              }
             }
           }
         }
       }
       if (i < n && !aborted(bs)) {
-        for (int c = 0; c < kC; ++c) {
-          cand_idx[int64_t(i) * kC + c] = c < st.cnt ? mli[c * kRB] : -1;
-          cand_val[int64_t(i) * kC + c] = c < st.cnt ? mlv[c * kRB] : -1.f;
+        for (int c = 0; c < kCH; ++c) {
+          cand_idx[int64_t(i) * kC + half * kCH + c] = c < st.cnt ? mli[c * kLists] : -1;
+          cand_val[int64_t(i) * kC + half * kCH + c] = c < st.cnt ? mlv[c * kLists] : -1.f;
         }
-        thr_out[i] = st.cnt >= kC ? st.minv : -1.f;
+        thr_out[int64_t(i) * 2 + half] = st.minv;  // -1 while the list was never full
       }
     }
   }
@@ -307,13 +325,13 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// rows x 64 bf16, row-major; box 128 rows x 64 (one 128-byte swizzle span)
-bool make_map(CUtensorMap* m, void* base, int64_t rows) {
+// rows x 64 bf16, row-major; box boxrows x 64 (one 128-byte swizzle span)
+bool make_map(CUtensorMap* m, void* base, int64_t rows, int boxrows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {cuuint64_t(kKP), cuuint64_t(rows)};
   cuuint64_t strides[1] = {cuuint64_t(kKP) * 2};
-  cuuint32_t box[2] = {cuuint32_t(kKP), cuuint32_t(kTM)};
+  cuuint32_t box[2] = {cuuint32_t(kKP), cuuint32_t(boxrows)};
   cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -339,10 +357,10 @@ cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, in
     prep_tc_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, A, B);
   }
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, d) || !make_map(&mb, B, d)) return cudaErrorInvalidValue;
+  if (!make_map(&ma, A, d, kTM) || !make_map(&mb, B, d, kTN)) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
   if (e != cudaSuccess) return e;
-  const int nrb = int((d + kRB - 1) / kRB);
+  const int nrb = int((d + kTM - 1) / kTM);
   const int grid = std::min(nrb, h->num_sms);
   const int ksteps = (r + 15) / 16;
   screen_tc_kernel<<<grid, kThreads, kSmemBytes, h->stream>>>(ma, mb, int(d), ksteps, cidx, cval, thr, h->d_status);
