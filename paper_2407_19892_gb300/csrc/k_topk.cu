@@ -162,13 +162,37 @@ __device__ __forceinline__ double vload(const void* V, int v64, int64_t idx) {
 
 __device__ __forceinline__ bool better(double a, int ja, double b, int jb) { return a > b || (a == b && ja < jb); }
 
+// (screened value, column) order of the candidate merge; empty slots are
+// (-1, INT_MAX) and sort last.
+__device__ __forceinline__ bool fbetter(float a, int ja, float b, int jb) { return a > b || (a == b && ja < jb); }
+
+// Bitonic sort of one (value, column) pair per lane across the warp,
+// descending or ascending in fbetter order.
+__device__ __forceinline__ void warp_sort_pairs(float& v, int& j, bool descending) {
+  const int lane = threadIdx.x & 31;
+  for (int size = 2; size <= 32; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, v, stride);
+      const int oj = __shfl_xor_sync(0xffffffffu, j, stride);
+      const bool desc = ((lane & size) == 0) == descending;
+      const bool take_better = ((lane & stride) == 0) == desc;
+      if (take_better != fbetter(v, j, ov, oj)) v = ov, j = oj;
+    }
+  }
+}
+
 // One warp per listed row: exact FP64 values of the kC candidates, warp
-// bitonic sort (|value| desc, column asc), certification, output.
+// bitonic sort (|value| desc, column asc), certification, output.  With two
+// candidate lists per row (nl = 2) the kC largest screened values of the
+// 2 kC are kept first (one list sorted descending, the other ascending, the
+// larger of each lane's pair: a bitonic split), and the largest dropped value
+// joins the row's thresholds: every column that is not rescored has a
+// screened value <= t.
 __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv, const double* __restrict__ psi,
                                int k, const int* __restrict__ rows, int64_t m_host, const int* __restrict__ count_dev,
                                const int32_t* __restrict__ cidx, const float* __restrict__ cval,
-                               const float* __restrict__ thr, int thr_n, const unsigned* __restrict__ colmax_bits,
-                               double u, int32_t* __restrict__ idx_out, float* __restrict__ val_out,
+                               const float* __restrict__ thr, int nl, const unsigned* __restrict__ colmax_bits, double u,
+                               int32_t* __restrict__ idx_out, float* __restrict__ val_out,
                                int* __restrict__ flag_list, int* __restrict__ flag_count,
                                unsigned* __restrict__ err_bits) {
   const int lane = threadIdx.x & 31;
@@ -177,13 +201,29 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t mi = w0; mi < m; mi += nw) {
     const int64_t i = rows ? int64_t(rows[mi]) : mi;
-    const int j = cidx[mi * kC + lane];
+    const int64_t cb = mi * (int64_t(kC) * nl);
+    int j = cidx[cb + lane];
+    float cv = cval[cb + lane];
+    double t = double(thr[mi * nl]);
+    if (nl == 2) {
+      int j2 = cidx[cb + kC + lane];
+      float cv2 = cval[cb + kC + lane];
+      if (j < 0) cv = -1.f, j = INT_MAX;
+      if (j2 < 0) cv2 = -1.f, j2 = INT_MAX;
+      warp_sort_pairs(cv, j, true);
+      warp_sort_pairs(cv2, j2, false);
+      const bool keep2 = fbetter(cv2, j2, cv, j);
+      const float dropped = keep2 ? cv : cv2;
+      if (keep2) cv = cv2, j = j2;
+      if (j == INT_MAX) j = -1;
+      t = fmax(fmax(t, double(thr[mi * nl + 1])), double(warp_max(dropped)));
+    }
     double ex = 0.0;
     if (j >= 0) {
       for (int q = 0; q < r; ++q) ex += vload(V, v64, i * ldv + q) * psi[q] * vload(V, v64, int64_t(j) * ldv + q);
     }
     // self-check of the screen: |screened - |exact|| must stay within the bound
-    const double serr = j >= 0 ? fabs(double(cval[mi * kC + lane]) - fabs(ex)) : 0.0;
+    const double serr = j >= 0 ? fabs(double(cv) - fabs(ex)) : 0.0;
     double key = j >= 0 ? fabs(ex) : -1.0;
     int kj = j >= 0 ? j : INT_MAX;
     double sv = ex;
@@ -217,10 +257,6 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
       if (lane == 0 && ratio > 0.0) atomicMax(err_bits, __float_as_uint(float(fmin(ratio, 1e30))));
     }
     const double qk = __shfl_sync(0xffffffffu, key, k - 1);
-    // the best excluded screened value: the largest of the row's list minima
-    // (-1 for a list that saw every one of its columns)
-    double t = double(thr[mi * thr_n]);
-    for (int q = 1; q < thr_n; ++q) t = fmax(t, double(thr[mi * thr_n + q]));
     const bool certified = t < 0.0 || qk > t + bnd;
     if (lane < k) {
       idx_out[i * k + lane] = kj == INT_MAX ? -1 : kj;
@@ -369,12 +405,12 @@ double screen_unit(gmgm_prec prec, int r) {
 
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
                     const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
-                    const float* thr, int thr_n, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
+                    const float* thr, int nl, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
                     int* flag_list, int* flag_count, unsigned* err_bits) {
   // one warp per row; the grid covers at most d rows (grid-stride beyond)
   const unsigned blocks = unsigned(std::min<int64_t>((d * 32 + 255) / 256, 65536));
-  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, cval, thr, thr_n,
-                                        colmax_bits, u, idx, val, flag_list, flag_count, err_bits);
+  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, cval, thr, nl, colmax_bits,
+                                        u, idx, val, flag_list, flag_count, err_bits);
 }
 
 // Exact FP64 top-k of the listed rows, column-parallel: a row's columns are
@@ -408,8 +444,8 @@ size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
   size_t b = 0;
   b += Carve::round(size_t(d) * rpad * 4) * 2;  // A, B
   b += Carve::round(size_t(r + 1) * 4);         // colmax + max row norm
-  b += Carve::round(size_t(d) * kC * 4) * 2;    // level-1 candidates
-  b += Carve::round(size_t(d) * 8);             // thresholds (up to two per row)
+  b += Carve::round(size_t(d) * kC * 8) * 2;    // candidates (up to two lists per row)
+  b += Carve::round(size_t(d) * 8);             // thresholds (one per list)
   b += Carve::round(size_t(d) * 4);             // flag list
   b += Carve::round(size_t(kExactCap) * 12) + 256;  // exact partial lists
   b += Carve::round(64);                        // counters
@@ -425,9 +461,12 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   float* A = c.take<float>(size_t(d) * rpad);
   float* B = c.take<float>(size_t(d) * rpad);
   unsigned* colmax = c.take<unsigned>(r + 1);  // [r] = max row norm
-  int32_t* cidx = c.take<int32_t>(size_t(d) * kC);
-  float* cval = c.take<float>(size_t(d) * kC);
-  float* thr = c.take<float>(2 * d);  // per row: one threshold (FP32 screen) or two (tensor-core screen)
+  // candidate lists per row: one from the FP32 screen, two (one per column
+  // half of a tile) from the tensor-core screen
+  const int nl = prec == GMGM_FP32 ? 1 : 2;
+  int32_t* cidx = c.take<int32_t>(size_t(d) * kC * 2);
+  float* cval = c.take<float>(size_t(d) * kC * 2);
+  float* thr = c.take<float>(size_t(d) * 2);
   int* flag1 = c.take<int>(d);
   double* part_v = c.take<double>(kExactCap);
   int* part_j = c.take<int>(kExactCap);
@@ -455,8 +494,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     GMGM_CUDA_TRY(h, launch_screen_tc(h, d, r, V, v_fp64, ldv, psi, prec, cidx, cval, thr, tc_scratch));
   }
   if (st) cudaEventRecord(ev[1], s);
-  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, prec == GMGM_FP32 ? 1 : 2,
-                 colmax, screen_unit(prec, r),
+  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, nl, colmax, screen_unit(prec, r),
                  idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
   note_launch(prec == GMGM_FP32 ? 4 : 3);
   // rows the screen could not certify: exact FP64 scan (the count is read
@@ -479,7 +517,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     memcpy(&e1, &hc[2], 4);
     st->rows_uncertified = int64_t(hc[0]);
     st->rows_exact = int64_t(nflag);
-    st->candidates = kC;
+    st->candidates = int64_t(kC) * nl;
     st->screen_ms = t1;
     st->rescore_ms = t2;
     st->screen_err_ratio = double(e1);

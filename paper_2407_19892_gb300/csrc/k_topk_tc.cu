@@ -9,16 +9,23 @@
 //               (K = 64 in four K=16 steps), FP32 in TMEM, double-buffered
 //               (2 x 256 of the 512 TMEM columns);
 //   warps 2-9   epilogue: two threads per row (one per 128-column half of the
-//               tile), each with a 16-slot candidate list; tcgen05.ld 32
+//               tile), each with a kC-slot candidate list; tcgen05.ld 32
 //               columns at a time, one max per element against the pair's
 //               shared threshold, and only when it is beaten a per-lane insert
 //               (a bitmask of the winners, values pulled out of registers by a
 //               select tree).
-// The pair's threshold is the larger of the two lists' minima (each list
-// publishes its minimum in shared memory once full); a stale read only admits
-// more candidates.  Every column left out of a row's two lists has a screened
-// value <= the larger final minimum, which is the row's certification
-// threshold.  All CTAs sweep the B tiles in the same order (L2 reuse).  Every
+// A list is four sub-lists of 8 slots with their minima cached, so replacing
+// the list's minimum rescans 8 slots, not 32.  Inserts are rare and
+// scattered over the lanes, so a lane that hits a chunk parks the chunk's 32
+// values in a shared-memory stash (one slot per thread) instead of inserting
+// at once; after each tile the warp drains the stashes together once 8 lanes
+// have one (a lane whose slot is taken inserts at once).  The pair's threshold is the
+// larger of the two lists' minima (each list publishes its minimum in shared
+// memory once full); a stale read only admits more candidates.  Every column
+// left out of a row's two lists has a screened value <= the larger final
+// minimum.  Each row gets 2 kC candidates and two thresholds; the rescore
+// keeps the kC largest screened values and folds the largest dropped one into
+// the row's certification threshold.  All CTAs sweep the B tiles in the same order (L2 reuse).  Every
 // wait is bounded; on timeout the kernel records GMGM_DEV_TIMEOUT and leaves
 // after freeing its TMEM.
 #include <cuda.h>
@@ -38,13 +45,17 @@ namespace {
 constexpr int kTM = 128;                     // rows per row block (MMA M)
 constexpr int kTN = 256;                     // columns per B tile (MMA N)
 constexpr int kKP = 64;                      // padded K (bf16 elements, one 128-byte row)
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kATile = kTM * kKP * 2;        // 16 KB
 constexpr int kBTile = kTN * kKP * 2;        // 32 KB
-constexpr int kCH = kC / 2;                  // slots per half-row list
+constexpr int kSub = 8;                      // slots per sub-list
+constexpr int kNSub = kC / kSub;             // sub-lists per list
 constexpr int kLists = 2 * kTM;              // (row, half) lists per CTA
+constexpr int kSlot = 36;                    // stash slot stride (words): 32 values, 16-byte aligned, 4-way banks
+constexpr int kBatch = 8;                    // stashed lanes that trigger a drain
+constexpr unsigned kFull = 0xffffffffu;
 constexpr long long kSpin = 1ll << 23;       // polls per bounded wait
 
 struct __align__(8) Bars {
@@ -60,7 +71,8 @@ struct __align__(8) Bars {
 };
 
 constexpr size_t kSmemBytes = 1024 /*align slack*/ + size_t(kATile) + size_t(kStages) * kBTile +
-                              size_t(2) * kCH * kLists * 4 + size_t(kLists) * 8 + sizeof(Bars);
+                              size_t(2) * kC * kLists * 4 + size_t(2) * kNSub * kLists * 4 + size_t(kLists) * 8 +
+                              size_t(32) * kEpiWarps * kSlot * 4 + sizeof(Bars);
 
 __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
   atomicExch(&bs->abort, 1);
@@ -70,10 +82,12 @@ __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
 __device__ __forceinline__ bool aborted(Bars* bs) { return *reinterpret_cast<volatile int*>(&bs->abort) != 0; }
 
 // One (row, half) candidate list, slot-major (stride kLists): fill, then
-// replace the minimum.  Out of line (inserts are rare); state by value.
+// replace the minimum.  Slots [8s, 8s+8) form sub-list s, whose minimum and
+// its slot sit in smv/smp (also slot-major).  Out of line (inserts are
+// rare); state by value.
 struct ListState {
   int cnt;
-  int minpos;
+  int minsub;  // sub-list holding the minimum
   float minv;  // minimum once full, else -1
 };
 
@@ -92,25 +106,86 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&r)[32], int e) {
   return (e & 1) ? d[1] : d[0];
 }
 
+// Minimum (value, slot) of sub-list sub.
+__device__ __forceinline__ void sub_min(const float* lv, int sub, float& mv, int& mp) {
+  mv = lv[(sub * kSub) * kLists];
+  mp = sub * kSub;
+#pragma unroll
+  for (int c = 1; c < kSub; ++c) {
+    const float x = lv[(sub * kSub + c) * kLists];
+    if (x < mv) mv = x, mp = sub * kSub + c;
+  }
+}
+
 // The published minimum carries the row block it belongs to (high word), so
 // a partner still in the previous row block is never mistaken for this one.
-__device__ __noinline__ ListState offer16(float* lv, int* li, unsigned long long* pub, unsigned tag, ListState st,
-                                          float v, int j) {
-  if (st.cnt < kCH) {
+__device__ __noinline__ ListState offer(float* lv, int* li, float* smv, int* smp, unsigned long long* pub, unsigned tag,
+                                        ListState st, float v, int j) {
+  if (st.cnt < kC) {
     lv[st.cnt * kLists] = v;
     li[st.cnt * kLists] = j;
-    ++st.cnt;
-    if (st.cnt < kCH) return st;
+    if (++st.cnt < kC) return st;
+#pragma unroll
+    for (int s = 0; s < kNSub; ++s) {
+      float mv;
+      int mp;
+      sub_min(lv, s, mv, mp);
+      smv[s * kLists] = mv;
+      smp[s * kLists] = mp;
+    }
   } else {
-    lv[st.minpos * kLists] = v;
-    li[st.minpos * kLists] = j;
+    const int s = st.minsub;
+    const int p = smp[s * kLists];
+    lv[p * kLists] = v;
+    li[p * kLists] = j;
+    float mv;
+    int mp;
+    sub_min(lv, s, mv, mp);
+    smv[s * kLists] = mv;
+    smp[s * kLists] = mp;
   }
-  st.minv = lv[0];
-  st.minpos = 0;
-  for (int c = 1; c < kCH; ++c)
-    if (lv[c * kLists] < st.minv) st.minv = lv[c * kLists], st.minpos = c;
+  st.minv = smv[0];
+  st.minsub = 0;
+#pragma unroll
+  for (int s = 1; s < kNSub; ++s) {
+    const float x = smv[s * kLists];
+    if (x < st.minv) st.minv = x, st.minsub = s;
+  }
   *reinterpret_cast<volatile unsigned long long*>(pub) =
       (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(st.minv);  // publish for the partner
+  return st;
+}
+
+__device__ __forceinline__ float partner_min(const volatile unsigned long long* partner, unsigned tag) {
+  const unsigned long long pv = *partner;
+  return unsigned(pv >> 32) == tag ? __uint_as_float(unsigned(pv)) : -1.f;
+}
+
+// Insert the winners of one stashed chunk (32 values, columns sj..sj+31)
+// against the current threshold.
+__device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int i, int n, float* lv, int* li, float* smv,
+                                        int* smp, unsigned long long* pub, const volatile unsigned long long* partner,
+                                        unsigned tag, ListState st) {
+  uint32_t v[32];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint4 w = reinterpret_cast<const uint4*>(slot)[k];
+    v[4 * k] = w.x, v[4 * k + 1] = w.y, v[4 * k + 2] = w.z, v[4 * k + 3] = w.w;
+  }
+  float thr = fmaxf(st.minv, partner_min(partner, tag));
+  uint32_t mask = 0;
+#pragma unroll
+  for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(v[e])) > thr ? 1u : 0u) << e;
+  while (mask) {
+    const int e = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const float x = fabsf(__uint_as_float(pick32(v, e)));
+    const int j = sj + e;
+    if (x > thr && j < n && j != i) {
+      st = offer(lv, li, smv, smp, pub, tag, st, x, j);
+      thr = fmaxf(st.minv, partner_min(partner, tag));
+    }
+  }
   return st;
 }
 
@@ -123,9 +198,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sA = smem;
   uint8_t* sB = sA + kATile;
   float* lv = reinterpret_cast<float*>(sB + kStages * kBTile);
-  int* li = reinterpret_cast<int*>(lv + kCH * kLists);
-  unsigned long long* pubs = reinterpret_cast<unsigned long long*>(li + kCH * kLists);  // [kLists] (tag, minimum)
-  Bars* bs = reinterpret_cast<Bars*>(pubs + kLists);
+  int* li = reinterpret_cast<int*>(lv + kC * kLists);
+  float* smv_all = reinterpret_cast<float*>(li + kC * kLists);        // [kNSub][kLists] sub-list minima
+  int* smp_all = reinterpret_cast<int*>(smv_all + kNSub * kLists);     // [kNSub][kLists] their slots
+  unsigned long long* pubs = reinterpret_cast<unsigned long long*>(smp_all + kNSub * kLists);  // [kLists] (tag, minimum)
+  uint32_t* stash = reinterpret_cast<uint32_t*>(pubs + kLists);  // [kEpiWarps * 32][kSlot]
+  Bars* bs = reinterpret_cast<Bars*>(stash + 32 * kEpiWarps * kSlot);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
@@ -140,6 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::prefetch_tmap(&tmA);
     tc::prefetch_tmap(&tmB);
   }
+  for (int L = threadIdx.x; L < kLists; L += blockDim.x) pubs[L] = ~0ull;  // no row block yet
   if (warp == 1) tc::tmem_alloc(&bs->tmem_base, 512);
   __syncthreads();
   tc::fence_after_sync();
@@ -220,22 +299,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int L = half * kTM + row_local;
     float* mlv = lv + L;
     int* mli = li + L;
+    float* msv = smv_all + L;
+    int* msp = smp_all + L;
     unsigned long long* mine = pubs + L;
     const volatile unsigned long long* partner = pubs + (1 - half) * kTM + row_local;
-    *reinterpret_cast<volatile unsigned long long*>(mine) = ~0ull;  // no row block yet
+    uint32_t* slot = stash + (ew * 32 + lane) * kSlot;
     long long accu = 0;
-    for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x) {
+    for (int rb = blockIdx.x; rb < nrb; rb += gridDim.x) {
+      if (__any_sync(kFull, aborted(bs))) break;
       const int i = rb * kTM + row_local;
       const unsigned tag = unsigned(rb);
       ListState st{0, 0, -1.f};
-      auto partner_min = [&]() {
-        const unsigned long long pv = *partner;
-        return unsigned(pv >> 32) == tag ? __uint_as_float(unsigned(pv)) : -1.f;
-      };
+      bool parked = false;  // this lane's stash slot holds a chunk
+      int sj = 0;           // its first column
+      bool ok = true;
       for (int t = 0; t < ntiles; ++t, ++accu) {
         const int b = int(accu & 1);
-        if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin)) {
-          raise_abort(bs, status);
+        ok = __all_sync(kFull, tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin));
+        if (!ok) {
+          if (lane == 0) raise_abort(bs, status);
           break;
         }
         tc::fence_after_sync();
@@ -251,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
-        float thr = fmaxf(st.minv, partner_min());
+        float thr = fmaxf(st.minv, partner_min(partner, tag));
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // four short max chains
@@ -263,29 +345,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             m3 = fmaxf(m3, fabsf(__uint_as_float(r[c][e + 3])));
           }
           if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr) {
-            uint32_t mask = 0;
+            if (!parked) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(r[c][e])) > thr ? 1u : 0u) << e;
-            while (mask) {
-              const int e = __ffs(mask) - 1;
-              mask &= mask - 1;
-              const float v = fabsf(__uint_as_float(pick32(r[c], e)));
-              const int j = j0 + c * 32 + e;
-              if (v > thr && j < n && j != i) {
-                st = offer16(mlv, mli, mine, tag, st, v, j);
-                thr = fmaxf(st.minv, partner_min());
+              for (int k = 0; k < 8; ++k)
+                reinterpret_cast<uint4*>(slot)[k] = make_uint4(r[c][4 * k], r[c][4 * k + 1], r[c][4 * k + 2], r[c][4 * k + 3]);
+              parked = true;
+              sj = j0 + c * 32;
+            } else {
+              uint32_t mask = 0;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(r[c][e])) > thr ? 1u : 0u) << e;
+              while (mask) {
+                const int e = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float v = fabsf(__uint_as_float(pick32(r[c], e)));
+                const int j = j0 + c * 32 + e;
+                if (v > thr && j < n && j != i) {
+                  st = offer(mlv, mli, msv, msp, mine, tag, st, v, j);
+                  thr = fmaxf(st.minv, partner_min(partner, tag));
+                }
               }
             }
           }
         }
+        if (__popc(__ballot_sync(kFull, parked)) >= kBatch) {
+          if (parked) st = drain(slot, sj, i, n, mlv, mli, msv, msp, mine, partner, tag, st);
+          parked = false;
+          __syncwarp();
+        }
       }
-      if (i < n && !aborted(bs)) {
-        for (int c = 0; c < kCH; ++c) {
-          cand_idx[int64_t(i) * kC + half * kCH + c] = c < st.cnt ? mli[c * kLists] : -1;
-          cand_val[int64_t(i) * kC + half * kCH + c] = c < st.cnt ? mlv[c * kLists] : -1.f;
+      if (!ok || __any_sync(kFull, aborted(bs))) break;
+      if (parked) st = drain(slot, sj, i, n, mlv, mli, msv, msp, mine, partner, tag, st);
+      if (i < n) {
+        for (int c = 0; c < kC; ++c) {
+          cand_idx[int64_t(i) * (2 * kC) + half * kC + c] = c < st.cnt ? mli[c * kLists] : -1;
+          cand_val[int64_t(i) * (2 * kC) + half * kC + c] = c < st.cnt ? mlv[c * kLists] : -1.f;
         }
         thr_out[int64_t(i) * 2 + half] = st.minv;  // -1 while the list was never full
       }
+      __syncwarp();
     }
   }
   __syncthreads();

@@ -46,7 +46,7 @@ double screen_unit(gmgm_prec prec, int r);
 // rescore + certify rows (all rows, or rows[] with a device-side count)
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
                     const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
-                    const float* thr, int thr_n, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
+                    const float* thr, int nl, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
                     int* flag_list, int* flag_count, unsigned* err_bits);
 
 // tensor-core screen (BF16 / 3xBF16) over all rows
