@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--k-cells", type=int, default=10)
     ap.add_argument("--k-genes", type=int, default=20)
     ap.add_argument("--gram-prec", default="bf16x3", choices=["fp32", "bf16x3"])
-    ap.add_argument("--topk-prec", default="bf16", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--topk-prec", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-warm-start", action="store_true",
                     help="start the eigenvalue solve at 1/E even when trained weights are present")
     ap.add_argument("--no-fp32-form", action="store_true",
@@ -236,9 +236,8 @@ def reference_arm(a, world, rank):
 
 def main():
     a = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2407_19892_gb300 import replicas
+    world, rank, local = replicas.rank_env()
     if a.impl == "reference":
         reference_arm(a, world, rank)
         return
@@ -257,7 +256,7 @@ def main():
     precs = {"fp32": g.FP32, "bf16": g.BF16, "bf16x3": g.BF16X3}
     gram_prec, topk_prec = precs[a.gram_prec], precs[a.topk_prec]
     split = gram_prec != g.FP32
-    counts = scrna_counts(a.cells, a.genes, a.clusters, seed=a.seed + rank, device=dev)
+    counts = scrna_counts(a.cells, a.genes, a.clusters, seed=replicas.replica_seed(a.seed, rank), device=dev)
     torch.cuda.synchronize()
     h = g.handle(dev)
     stream = torch.cuda.current_stream(dev)
@@ -310,9 +309,7 @@ def main():
         return out, ws_info
 
     def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        replicas.barrier(dev)
 
     for _ in range(a.warmup):
         res = step(counts)
@@ -335,12 +332,8 @@ def main():
     barrier()
     launches = (lib.gmgm_kernel_launches() - launches0) // a.steps
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.cells / (ms / 1e3)
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    value = replicas.job_throughput(a.cells, world, ms)
     solve = res.solve
     unc = int(res.topk_rows_stats["rows_uncertified"])
 
@@ -369,12 +362,8 @@ def main():
             gval_h.copy_(r2.val_cols, non_blocking=True)
         q1.record(stream)
         barrier()
-        ems = q0.elapsed_time(q1) / n_e2e
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * a.cells / (ems / 1e3), "unit": UNIT,
+        ems = replicas.max_over_ranks(q0.elapsed_time(q1) / n_e2e, dev)
+        e2e = {"value": replicas.job_throughput(a.cells, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": host.numel() * 4,
                "d2h_bytes_per_step": (idx_h.numel() + val_h.numel() + gidx_h.numel() + gval_h.numel()) * 4}
         del host, dev_in
@@ -429,7 +418,7 @@ def main():
                "sample": f"first {n_s} cells of the same matrix; cell top-k timed on {a.cpu_sample_rows} rows; "
                          f"stages extrapolated to {a.cells} cells by complexity ({sample_s:.1f} s of CPU work)",
                "stage_s": {k: round(v, 3) for k, v in full.items()}}
-    dtype = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[a.topk_prec]
+    dtype = {"fp32": "f32", "bf16": "bf16"}[a.topk_prec]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -443,6 +432,7 @@ def main():
         "clocks": clocks,
         "detail": {"stage_ms": stage_ms, "warm_start": warm_info, "fp32_form": fp32_form, "solve": solve,
                    "rows_uncertified": unc,
+                   "rows_exact": int(res.topk_rows_stats["rows_exact"]),
                    "screen_ms": scr_ms,
                    "gene_topk": res.topk_cols_stats},
     }

@@ -358,8 +358,8 @@ typedef struct {
  *           leading dimension ldv >= r.
  *   psi     device, r FP64 eigenvalues.
  *   k       1 <= k <= 32 and k < d.
- *   prec    screen arithmetic: GMGM_FP32 (SIMT), GMGM_BF16 or GMGM_BF16X3
- *           (tcgen05 tensor cores).
+ *   prec    screen arithmetic: GMGM_FP32 (SIMT) or GMGM_BF16 (tcgen05 tensor
+ *           cores, r <= 64); any other value is GMGM_E_ARG.
  *   idx_out device, d x k int32: column indices, by |Psi_ij| descending.
  *   val_out device, d x k FP32: the signed Psi_ij, computed in FP64 from V
  *           (as given) and psi, then rounded.

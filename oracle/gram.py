@@ -19,6 +19,31 @@ def log1p_centre(counts: np.ndarray) -> np.ndarray:
     return x - x.mean(axis=0, keepdims=True)
 
 
+def log1p_col_means(chunks, threads: int = 8) -> np.ndarray:
+    """The column means that ``log1p_centre`` subtracts, for a matrix given as
+    row blocks (``chunks`` yields array-likes with the same columns): each
+    block's FP64 column sums of log1p, added, over the total row count.  Row
+    blocks only split the sum over cells; ``threads`` blocks are summed at a
+    time (numpy releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def part(c):
+        y = np.log1p(np.asarray(c, dtype=np.float64))
+        return y.sum(axis=0), y.shape[0]
+
+    total, n = None, 0
+    it = iter(chunks)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        while True:
+            wave = [c for _, c in zip(range(threads), it)]  # at most `threads` blocks held at once
+            if not wave:
+                break
+            for s, m in ex.map(part, wave):
+                total = s if total is None else total + s
+                n += m
+    return total / n
+
+
 def matricize(t: np.ndarray, axis: int) -> np.ndarray:
     """mat_l[T]: move ``axis`` to the front and flatten the rest (row-major),
     giving a d_l x (prod of the other sizes) matrix."""

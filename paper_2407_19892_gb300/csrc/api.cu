@@ -353,8 +353,8 @@ int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v
   if (k < 1 || k > 32 || k >= d) return fail(h, GMGM_E_ARG, "gmgm_topk_network: need 1 <= k <= 32, k < d");
   if (d > (int64_t(1) << 31) - 1) return fail(h, GMGM_E_ARG, "gmgm_topk_network: d >= 2^31");
   if (r > 4096) return fail(h, GMGM_E_ARG, "gmgm_topk_network: r > 4096");
-  if (prec != GMGM_FP32 && prec != GMGM_BF16 && prec != GMGM_BF16X3)
-    return fail(h, GMGM_E_ARG, "gmgm_topk_network: prec must be FP32, BF16 or BF16X3");
+  if (prec != GMGM_FP32 && prec != GMGM_BF16)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network: prec must be FP32 or BF16");
   if (prec != GMGM_FP32 && r > 64)
     return fail(h, GMGM_E_ARG, "gmgm_topk_network: tensor-core screen supports r <= 64");
   GMGM_CUDA_TRY(h, cudaSetDevice(h->device));

@@ -7,8 +7,12 @@
 //
 // Work item = (output tile 128 genes x 256 genes of the upper triangle,
 // K range of the cells).  The tensor core's FP32 accumulation is kept short:
-// the accumulator is drained every kSub K blocks (2048 cells) into an FP64
-// running tile owned by the CTA.  Persistent CTAs, warp-specialised:
+// the accumulator is drained every kSub K blocks (1024 cells) into an FP64
+// running tile owned by the CTA.  Its rounding error grows with the length
+// of a block (measured at 1M cells x 2000 genes against an FP64 Gram of the
+// same X: 3.7e-5 of max|S| with 2048-cell blocks, 1.85e-5 with 1024, 9.7e-6
+// with 512; the FP32 SIMT Gram reaches 3.2e-5); 1024 cells costs +20% time
+// over 2048, 512 cells +70%.  Persistent CTAs, warp-specialised:
 //   warp 0      TMA producer: per K block the A (128 rows) and B (256 rows)
 //               slices of hi (and lo) into a 2-stage ring;
 //   warp 1      MMA issuer: tcgen05.mma M=128 N=256 K=16, FP32 accumulator
@@ -33,7 +37,7 @@ namespace {
 
 constexpr int kGM = 128;                     // tile rows (genes a)
 constexpr int kGN = 256;                     // tile cols (genes b)
-constexpr int kSub = 32;                     // 64-cell K blocks per accumulator drain
+constexpr int kSub = 16;                     // 64-cell K blocks per accumulator drain
 constexpr int kGStages = 2;
 constexpr int kGThreads = 64 + 128;
 constexpr int kABytes = kGM * 128;           // 16 KB per plane

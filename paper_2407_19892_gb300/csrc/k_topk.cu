@@ -181,19 +181,34 @@ __device__ __forceinline__ void warp_sort_pairs(float& v, int& j, bool descendin
   }
 }
 
+// Bitonic merge of a bitonic sequence (one pair per lane) into descending
+// fbetter order.
+__device__ __forceinline__ void warp_merge_desc(float& v, int& j) {
+  const int lane = threadIdx.x & 31;
+  for (int stride = 16; stride > 0; stride >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, stride);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, stride);
+    const bool take_better = (lane & stride) == 0;
+    if (take_better != fbetter(v, j, ov, oj)) v = ov, j = oj;
+  }
+}
+
 // One warp per listed row: exact FP64 values of the kC candidates, warp
-// bitonic sort (|value| desc, column asc), certification, output.  With two
-// candidate lists per row (nl = 2) the kC largest screened values of the
-// 2 kC are kept first (one list sorted descending, the other ascending, the
-// larger of each lane's pair: a bitonic split), and the largest dropped value
-// joins the row's thresholds: every column that is not rescored has a
-// screened value <= t.
+// bitonic sort (|value| desc, column asc), certification, output.
+// Candidate lists: nl = 1 (FP32 screen): cidx/cval[mi][kC], thr[mi];
+// nl = 2 ncs (tensor-core screens: two column halves x ncs column slices):
+// list l of row mi at [(l / 2) * lstride + mi][2 kC] + (l % 2) kC, its
+// minimum at thr[((l / 2) * lstride + mi) * 2 + l % 2].  Several lists are
+// merged pairwise, keeping the kC largest screened values (the running list
+// descending, the next ascending, the larger of each lane's pair: a bitonic
+// split), and every dropped value joins the row's threshold t: every column
+// that is not rescored has a screened value <= t.
 __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t ldv, const double* __restrict__ psi,
                                int k, const int* __restrict__ rows, int64_t m_host, const int* __restrict__ count_dev,
                                const int32_t* __restrict__ cidx, const float* __restrict__ cval,
-                               const float* __restrict__ thr, int nl, const unsigned* __restrict__ colmax_bits, double u,
-                               int32_t* __restrict__ idx_out, float* __restrict__ val_out,
-                               int* __restrict__ flag_list, int* __restrict__ flag_count,
+                               const float* __restrict__ thr, int nl, int64_t lstride,
+                               const unsigned* __restrict__ colmax_bits, double u, int32_t* __restrict__ idx_out,
+                               float* __restrict__ val_out, int* __restrict__ flag_list, int* __restrict__ flag_count,
                                unsigned* __restrict__ err_bits) {
   const int lane = threadIdx.x & 31;
   const int64_t m = count_dev ? int64_t(*count_dev) : m_host;
@@ -201,22 +216,35 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t mi = w0; mi < m; mi += nw) {
     const int64_t i = rows ? int64_t(rows[mi]) : mi;
-    const int64_t cb = mi * (int64_t(kC) * nl);
-    int j = cidx[cb + lane];
-    float cv = cval[cb + lane];
-    double t = double(thr[mi * nl]);
-    if (nl == 2) {
-      int j2 = cidx[cb + kC + lane];
-      float cv2 = cval[cb + kC + lane];
-      if (j < 0) cv = -1.f, j = INT_MAX;
-      if (j2 < 0) cv2 = -1.f, j2 = INT_MAX;
-      warp_sort_pairs(cv, j, true);
-      warp_sort_pairs(cv2, j2, false);
-      const bool keep2 = fbetter(cv2, j2, cv, j);
-      const float dropped = keep2 ? cv : cv2;
-      if (keep2) cv = cv2, j = j2;
+    int j;
+    float cv;
+    double t;
+    if (nl == 1) {
+      j = cidx[mi * kC + lane];
+      cv = cval[mi * kC + lane];
+      t = double(thr[mi]);
+    } else {
+      t = -1.0;
+      for (int l = 0; l < nl; ++l) {
+        const int64_t pair = int64_t(l >> 1) * lstride + mi;
+        const int64_t base = pair * (2 * kC) + (l & 1) * kC;
+        int j2 = cidx[base + lane];
+        float v2 = cval[base + lane];
+        if (j2 < 0) v2 = -1.f, j2 = INT_MAX;
+        t = fmax(t, double(thr[pair * 2 + (l & 1)]));
+        if (l == 0) {
+          cv = v2, j = j2;
+          warp_sort_pairs(cv, j, true);
+          continue;
+        }
+        warp_sort_pairs(v2, j2, false);
+        const bool keep2 = fbetter(v2, j2, cv, j);
+        const float dropped = keep2 ? cv : v2;
+        if (keep2) cv = v2, j = j2;
+        t = fmax(t, double(warp_max(dropped)));
+        if (l + 1 < nl) warp_merge_desc(cv, j);
+      }
       if (j == INT_MAX) j = -1;
-      t = fmax(fmax(t, double(thr[mi * nl + 1])), double(warp_max(dropped)));
     }
     double ex = 0.0;
     if (j >= 0) {
@@ -393,24 +421,26 @@ constexpr int64_t kExactCap = int64_t(1) << 22;  // partial entries held at once
 double screen_unit(gmgm_prec prec, int r) {
   const double u32 = 1.0 / 16777216.0;  // 2^-24
   const double kf = 1.02;               // slack over the first-order bound
+  const double ub = 1.0 / 256.0;        // BF16 unit roundoff: 8 significant bits, 2^-8
   // FP32 SIMT: operand rounding (2u) + FMA accumulation of r terms (r u).
-  // Tensor cores: operand rounding to BF16 (hi only: 2 * 2^-9; split: the
-  // dropped lo*lo and rounding of lo, 3 * 2^-18) + an accumulation of K
-  // products whose additions are each charged 2u (the tensor core's internal
-  // alignment/rounding is not IEEE round-to-nearest).
+  // Tensor cores: both operands rounded to BF16 (2 ub + ub^2 per product)
+  // + an accumulation of K products whose additions are each charged 2u
+  // (the tensor core's internal alignment/rounding is not IEEE
+  // round-to-nearest).  The split form (hi + lo, lo*lo dropped) would leave
+  // 3 ub^2 per product.
   if (prec == GMGM_FP32) return kf * (double(r) + 4.0) * u32;
-  if (prec == GMGM_BF16) return kf * (2.0 / 512.0 + 2.0 * (double(r) + 4.0) * u32);
-  return kf * (3.0 / 262144.0 + 2.0 * (3.0 * double(r) + 4.0) * u32);
+  if (prec == GMGM_BF16) return kf * (2.0 * ub + ub * ub + 2.0 * (double(r) + 4.0) * u32);
+  return kf * (3.0 * ub * ub + 2.0 * (3.0 * double(r) + 4.0) * u32);
 }
 
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
                     const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
-                    const float* thr, int nl, const unsigned* colmax_bits, double u, int32_t* idx, float* val,
-                    int* flag_list, int* flag_count, unsigned* err_bits) {
-  // one warp per row; the grid covers at most d rows (grid-stride beyond)
-  const unsigned blocks = unsigned(std::min<int64_t>((d * 32 + 255) / 256, 65536));
-  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, d, count_dev, cidx, cval, thr, nl, colmax_bits,
-                                        u, idx, val, flag_list, flag_count, err_bits);
+                    const float* thr, int nl, int64_t lstride, int64_t m, const unsigned* colmax_bits, double u,
+                    int32_t* idx, float* val, int* flag_list, int* flag_count, unsigned* err_bits) {
+  // one warp per row; the grid covers at most m rows (grid-stride beyond)
+  const unsigned blocks = unsigned(std::min<int64_t>((m * 32 + 255) / 256, 65536));
+  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, m, count_dev, cidx, cval, thr, nl, lstride,
+                                        colmax_bits, u, idx, val, flag_list, flag_count, err_bits);
 }
 
 // Exact FP64 top-k of the listed rows, column-parallel: a row's columns are
@@ -446,7 +476,7 @@ size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
   b += Carve::round(size_t(r + 1) * 4);         // colmax + max row norm
   b += Carve::round(size_t(d) * kC * 8) * 2;    // candidates (up to two lists per row)
   b += Carve::round(size_t(d) * 8);             // thresholds (one per list)
-  b += Carve::round(size_t(d) * 4);             // flag list
+  b += Carve::round(size_t(d) * 4) * 2;         // flag lists (first screen, repair)
   b += Carve::round(size_t(kExactCap) * 12) + 256;  // exact partial lists
   b += Carve::round(64);                        // counters
   b += Carve::round(topk_tc_scratch_bytes(d, r, prec));
@@ -468,6 +498,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   float* cval = c.take<float>(size_t(d) * kC * 2);
   float* thr = c.take<float>(size_t(d) * 2);
   int* flag1 = c.take<int>(d);
+  int* flag2 = c.take<int>(d);
   double* part_v = c.take<double>(kExactCap);
   int* part_j = c.take<int>(kExactCap);
   int* counters = c.take<int>(16);
@@ -494,15 +525,30 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     GMGM_CUDA_TRY(h, launch_screen_tc(h, d, r, V, v_fp64, ldv, psi, prec, cidx, cval, thr, tc_scratch));
   }
   if (st) cudaEventRecord(ev[1], s);
-  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, nl, colmax, screen_unit(prec, r),
-                 idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
+  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, nl, d, d, colmax,
+                 screen_unit(prec, r), idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
   note_launch(prec == GMGM_FP32 ? 4 : 3);
-  // rows the screen could not certify: exact FP64 scan (the count is read
-  // back once to size the work)
-  int nflag = 0;
+  // rows the screen could not certify (the count is read back once to size
+  // the work): after the BF16 screen, a 3xBF16 tensor-core screen of those
+  // rows and a second certification; what remains, an exact FP64 scan
+  int nflag = 0, nexact = 0;
   GMGM_CUDA_TRY(h, cudaMemcpyAsync(&nflag, counters, sizeof(int), cudaMemcpyDeviceToHost, s));
   GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
-  int rc = run_exact_rows(h, d, r, V, v_fp64, ldv, psi, k, flag1, nflag, part_v, part_j, idx, val);
+  const int* exact_rows = flag1;
+  nexact = nflag;
+  if (prec == GMGM_BF16 && nflag > 0) {
+    const int ncs = screen_tc_slices(nflag, h->num_sms, d);
+    GMGM_CUDA_TRY(h, launch_screen_tc_repair(h, d, r, V, v_fp64, ldv, psi, flag1, nflag, ncs, cidx, cval, thr,
+                                             tc_scratch));
+    launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, flag1, nullptr, cidx, cval, thr, 2 * ncs, nflag, nflag, colmax,
+                   screen_unit(GMGM_BF16X3, r), idx, val, flag2, counters + 4,
+                   reinterpret_cast<unsigned*>(counters + 2));
+    note_launch(1);
+    GMGM_CUDA_TRY(h, cudaMemcpyAsync(&nexact, counters + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
+    exact_rows = flag2;
+  }
+  int rc = run_exact_rows(h, d, r, V, v_fp64, ldv, psi, k, exact_rows, nexact, part_v, part_j, idx, val);
   if (rc) return rc;
   if (st) cudaEventRecord(ev[2], s);
   GMGM_CUDA_TRY(h, cudaGetLastError());
@@ -516,7 +562,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     float e1;
     memcpy(&e1, &hc[2], 4);
     st->rows_uncertified = int64_t(hc[0]);
-    st->rows_exact = int64_t(nflag);
+    st->rows_exact = int64_t(nexact);
     st->candidates = int64_t(kC) * nl;
     st->screen_ms = t1;
     st->rescore_ms = t2;

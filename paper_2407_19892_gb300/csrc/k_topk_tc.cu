@@ -1,33 +1,38 @@
-// Tensor-core screen for the per-row top-k of Psi = V diag(psi) V^T
+// Tensor-core screens for the per-row top-k of Psi = V diag(psi) V^T
 // (Algorithm 1: threshold simultaneously with recomposition), sm_103a.
 //
-// Persistent, warp-specialised kernel, one CTA per SM:
-//   warp 0      TMA producer: the CTA's 128 A rows (bf16(V psi)) once per row
-//               block, then every B tile (bf16(V), 256 rows) into a 4-stage
-//               shared-memory ring;
-//   warp 1      MMA issuer (one thread): per B tile D[128 x 256] = A B^T
-//               (K = 64 in four K=16 steps), FP32 in TMEM, double-buffered
-//               (2 x 256 of the 512 TMEM columns);
-//   warps 2-9   epilogue: two threads per row (one per 128-column half of the
-//               tile), each with a kC-slot candidate list; tcgen05.ld 32
+// One kernel template, two instances:
+//   main screen    BF16 operands (one product per K step), 128 x 256 tiles,
+//                  over every row;
+//   repair screen  3xBF16 split products (hi.hi + hi.lo + lo.hi: ~120x
+//                  tighter error bound), 128 x 128 tiles, over the rows the
+//                  main screen could not certify.
+// Persistent, warp-specialised, one CTA per SM:
+//   warp 0      TMA producer: the CTA's 128 A rows once per row block, then
+//               every B tile into a 3-stage shared-memory ring;
+//   warp 1      MMA issuer (one thread): per B tile D[128 x TN] = A B^T
+//               (K = 64 in four K=16 steps), FP32 in TMEM, double-buffered;
+//   warps 2-9   epilogue: two threads per row (one per half of the tile's
+//               columns), each with a kC-slot candidate list; tcgen05.ld 32
 //               columns at a time, one max per element against the pair's
 //               shared threshold, and only when it is beaten a per-lane insert
 //               (a bitmask of the winners, values pulled out of registers by a
 //               select tree).
 // A list is four sub-lists of 8 slots with their minima cached, so replacing
-// the list's minimum rescans 8 slots, not 32.  Inserts are rare and
-// scattered over the lanes, so a lane that hits a chunk parks the chunk's 32
-// values in a shared-memory stash (one slot per thread) instead of inserting
-// at once; after each tile the warp drains the stashes together once 8 lanes
-// have one (a lane whose slot is taken inserts at once).  The pair's threshold is the
-// larger of the two lists' minima (each list publishes its minimum in shared
-// memory once full); a stale read only admits more candidates.  Every column
-// left out of a row's two lists has a screened value <= the larger final
-// minimum.  Each row gets 2 kC candidates and two thresholds; the rescore
-// keeps the kC largest screened values and folds the largest dropped one into
-// the row's certification threshold.  All CTAs sweep the B tiles in the same order (L2 reuse).  Every
-// wait is bounded; on timeout the kernel records GMGM_DEV_TIMEOUT and leaves
-// after freeing its TMEM.
+// the list's minimum rescans 8 slots, not 32.  In the main screen inserts are
+// rare and scattered over the lanes, so a lane that hits a chunk parks the
+// chunk's 32 values in a shared-memory stash (one slot per thread) instead of
+// inserting at once; after each tile the warp drains the stashes together
+// once 8 lanes have one (a lane whose slot is taken inserts at once).  The
+// pair's threshold is the larger of the two lists' minima (each list
+// publishes its minimum in shared memory once full); a stale read only admits
+// more candidates.  Every column left out of a row's two lists has a screened
+// value <= the larger final minimum.  Each row gets 2 kC candidates and two
+// thresholds; the rescore keeps the kC largest screened values and folds the
+// largest dropped one into the row's certification threshold.  All CTAs sweep
+// the B tiles in the same order (L2 reuse).  Every wait is bounded; on
+// timeout the kernel records GMGM_DEV_TIMEOUT and leaves after freeing its
+// TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -43,13 +48,11 @@ namespace gmgm {
 namespace {
 
 constexpr int kTM = 128;                     // rows per row block (MMA M)
-constexpr int kTN = 256;                     // columns per B tile (MMA N)
 constexpr int kKP = 64;                      // padded K (bf16 elements, one 128-byte row)
 constexpr int kStages = 3;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kATile = kTM * kKP * 2;        // 16 KB
-constexpr int kBTile = kTN * kKP * 2;        // 32 KB
+constexpr int kATile = kTM * kKP * 2;        // 16 KB per plane
 constexpr int kSub = 8;                      // slots per sub-list
 constexpr int kNSub = kC / kSub;             // sub-lists per list
 constexpr int kLists = 2 * kTM;              // (row, half) lists per CTA
@@ -57,6 +60,19 @@ constexpr int kSlot = 36;                    // stash slot stride (words): 32 va
 constexpr int kBatch = 8;                    // stashed lanes that trigger a drain
 constexpr unsigned kFull = 0xffffffffu;
 constexpr long long kSpin = 1ll << 23;       // polls per bounded wait
+
+// TN columns per B tile; NP products per K step (1: BF16, 3: split);
+// STASH: park hit chunks for batched inserts.
+template <int TN, int NP, bool STASH>
+struct Screen {
+  static constexpr int kTN = TN;
+  static constexpr int kChunks = TN / 64;                 // 32-column chunks per half
+  static constexpr int kPlanes = NP == 3 ? 2 : 1;         // hi (+ lo)
+  static constexpr int kBTile = TN * kKP * 2;             // per plane
+  static constexpr int kTmemCols = 2 * TN;
+  static constexpr size_t kLists_ = size_t(2) * kC * kLists * 4 + size_t(2) * kNSub * kLists * 4 + size_t(kLists) * 8;
+  static constexpr size_t kStash = STASH ? size_t(32) * kEpiWarps * kSlot * 4 : 0;
+};
 
 struct __align__(8) Bars {
   uint64_t full[kStages];
@@ -70,9 +86,11 @@ struct __align__(8) Bars {
   int abort;
 };
 
-constexpr size_t kSmemBytes = 1024 /*align slack*/ + size_t(kATile) + size_t(kStages) * kBTile +
-                              size_t(2) * kC * kLists * 4 + size_t(2) * kNSub * kLists * 4 + size_t(kLists) * 8 +
-                              size_t(32) * kEpiWarps * kSlot * 4 + sizeof(Bars);
+template <class S>
+constexpr size_t smem_bytes() {
+  return 1024 /*align slack*/ + size_t(S::kPlanes) * kATile + size_t(kStages) * S::kPlanes * S::kBTile + S::kLists_ +
+         S::kStash + sizeof(Bars);
+}
 
 __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
   atomicExch(&bs->abort, 1);
@@ -161,17 +179,12 @@ __device__ __forceinline__ float partner_min(const volatile unsigned long long* 
   return unsigned(pv >> 32) == tag ? __uint_as_float(unsigned(pv)) : -1.f;
 }
 
-// Insert the winners of one stashed chunk (32 values, columns sj..sj+31)
-// against the current threshold.
-__device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int i, int n, float* lv, int* li, float* smv,
-                                        int* smp, unsigned long long* pub, const volatile unsigned long long* partner,
-                                        unsigned tag, ListState st) {
-  uint32_t v[32];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const uint4 w = reinterpret_cast<const uint4*>(slot)[k];
-    v[4 * k] = w.x, v[4 * k + 1] = w.y, v[4 * k + 2] = w.z, v[4 * k + 3] = w.w;
-  }
+// Insert the winners of one 32-value chunk (columns sj..sj+31) against the
+// current threshold; `self` is the row's own column (never an edge).
+__device__ __forceinline__ ListState insert_chunk(const uint32_t (&v)[32], int sj, int self, int n, float* lv, int* li,
+                                                  float* smv, int* smp, unsigned long long* pub,
+                                                  const volatile unsigned long long* partner, unsigned tag,
+                                                  ListState st) {
   float thr = fmaxf(st.minv, partner_min(partner, tag));
   uint32_t mask = 0;
 #pragma unroll
@@ -181,7 +194,7 @@ __device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int i, int
     mask &= mask - 1;
     const float x = fabsf(__uint_as_float(pick32(v, e)));
     const int j = sj + e;
-    if (x > thr && j < n && j != i) {
+    if (x > thr && j < n && j != self) {
       st = offer(lv, li, smv, smp, pub, tag, st, x, j);
       thr = fmaxf(st.minv, partner_min(partner, tag));
     }
@@ -189,21 +202,42 @@ __device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int i, int
   return st;
 }
 
+// A stashed chunk (shared memory) through insert_chunk.
+__device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int self, int n, float* lv, int* li, float* smv,
+                                        int* smp, unsigned long long* pub, const volatile unsigned long long* partner,
+                                        unsigned tag, ListState st) {
+  uint32_t v[32];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint4 w = reinterpret_cast<const uint4*>(slot)[k];
+    v[4 * k] = w.x, v[4 * k + 1] = w.y, v[4 * k + 2] = w.z, v[4 * k + 3] = w.w;
+  }
+  return insert_chunk(v, sj, self, n, lv, li, smv, smp, pub, partner, tag, st);
+}
+
+// m rows of A (hi, lo planes) against n rows of B (hi, lo planes), the B
+// tiles split into ncs column slices; work item = (row block, slice).  Row p
+// of A is row rows[p] of Psi (p itself when rows is null); slice cs writes
+// its two lists of row p to cand_*[cs * m + p][2 kC] and their minima to
+// thr_out[cs * m + p][2].
+template <int TN, int NP, bool STASH>
 __global__ void __launch_bounds__(kThreads, 1)
-    screen_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n,
-                     int ksteps, int32_t* __restrict__ cand_idx, float* __restrict__ cand_val,
-                     float* __restrict__ thr_out, int* __restrict__ status) {
+    screen_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int m, int n,
+                     int ncs, const int* __restrict__ rows, int ksteps, int32_t* __restrict__ cand_idx,
+                     float* __restrict__ cand_val, float* __restrict__ thr_out, int* __restrict__ status) {
+  using S = Screen<TN, NP, STASH>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = smem;
-  uint8_t* sB = sA + kATile;
-  float* lv = reinterpret_cast<float*>(sB + kStages * kBTile);
+  uint8_t* sA = smem;                                  // [kPlanes][kATile]
+  uint8_t* sB = sA + S::kPlanes * kATile;              // [kStages][kPlanes][kBTile]
+  float* lv = reinterpret_cast<float*>(sB + kStages * S::kPlanes * S::kBTile);
   int* li = reinterpret_cast<int*>(lv + kC * kLists);
   float* smv_all = reinterpret_cast<float*>(li + kC * kLists);        // [kNSub][kLists] sub-list minima
   int* smp_all = reinterpret_cast<int*>(smv_all + kNSub * kLists);     // [kNSub][kLists] their slots
   unsigned long long* pubs = reinterpret_cast<unsigned long long*>(smp_all + kNSub * kLists);  // [kLists] (tag, minimum)
-  uint32_t* stash = reinterpret_cast<uint32_t*>(pubs + kLists);  // [kEpiWarps * 32][kSlot]
-  Bars* bs = reinterpret_cast<Bars*>(stash + 32 * kEpiWarps * kSlot);
+  uint32_t* stash = reinterpret_cast<uint32_t*>(pubs + kLists);       // [kEpiWarps * 32][kSlot] (STASH)
+  Bars* bs = reinterpret_cast<Bars*>(reinterpret_cast<uint8_t*>(stash) + S::kStash);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
@@ -215,38 +249,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::fence_barrier_init();
   }
   if (warp == 0 && lane == 0) {
-    tc::prefetch_tmap(&tmA);
-    tc::prefetch_tmap(&tmB);
+    tc::prefetch_tmap(&tmAh);
+    tc::prefetch_tmap(&tmBh);
+    if (NP == 3) {
+      tc::prefetch_tmap(&tmAl);
+      tc::prefetch_tmap(&tmBl);
+    }
   }
   for (int L = threadIdx.x; L < kLists; L += blockDim.x) pubs[L] = ~0ull;  // no row block yet
-  if (warp == 1) tc::tmem_alloc(&bs->tmem_base, 512);
+  if (warp == 1) tc::tmem_alloc(&bs->tmem_base, S::kTmemCols);
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = bs->tmem_base;
-  const int nrb = (n + kTM - 1) / kTM;
-  const int ntiles = (n + kTN - 1) / kTN;
+  const int nrb = (m + kTM - 1) / kTM;
+  const int ntiles = (n + TN - 1) / TN;
+  const int items = nrb * ncs;
+  const int per_slice = (ntiles + ncs - 1) / ncs;  // B tiles per column slice
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       long long issued = 0;
       int rbi = 0;
-      for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x, ++rbi) {
+      for (int w = blockIdx.x; w < items && !aborted(bs); w += gridDim.x, ++rbi) {
+        const int rb = w / ncs, cs = w - rb * ncs;
+        const int t0 = cs * per_slice, t1 = min(ntiles, t0 + per_slice);
         if (!tc::mbar_wait(&bs->aempty, (rbi & 1) ^ 1, kSpin)) {
           raise_abort(bs, status);
           break;
         }
-        tc::mbar_arrive_expect_tx(&bs->afull, kATile);
-        tc::tma_load_2d(sA, &tmA, &bs->afull, 0, rb * kTM);
-        for (int t = 0; t < ntiles; ++t, ++issued) {
+        tc::mbar_arrive_expect_tx(&bs->afull, S::kPlanes * kATile);
+        tc::tma_load_2d(sA, &tmAh, &bs->afull, 0, rb * kTM);
+        if (NP == 3) tc::tma_load_2d(sA + kATile, &tmAl, &bs->afull, 0, rb * kTM);
+        for (int t = t0; t < t1; ++t, ++issued) {
           const int s = int(issued % kStages);
           const uint32_t k = uint32_t(issued / kStages);
           if (!tc::mbar_wait(&bs->empty[s], (k & 1) ^ 1, kSpin)) {
             raise_abort(bs, status);
             break;
           }
-          tc::mbar_arrive_expect_tx(&bs->full[s], kBTile);
-          tc::tma_load_2d(sB + s * kBTile, &tmB, &bs->full[s], 0, t * kTN);
+          uint8_t* dst = sB + s * S::kPlanes * S::kBTile;
+          tc::mbar_arrive_expect_tx(&bs->full[s], S::kPlanes * S::kBTile);
+          tc::tma_load_2d(dst, &tmBh, &bs->full[s], 0, t * TN);
+          if (NP == 3) tc::tma_load_2d(dst + S::kBTile, &tmBl, &bs->full[s], 0, t * TN);
         }
         if (aborted(bs)) break;
       }
@@ -259,16 +304,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = tc::idesc_bf16_f32(kTM, kTN);
-      const uint32_t abase = tc::smem_u32(sA);
+      const uint32_t idesc = tc::idesc_bf16_f32(kTM, TN);
+      const uint32_t ah = tc::smem_u32(sA), al = ah + kATile;
       long long used = 0, accu = 0;
       int rbi = 0;
-      for (int rb = blockIdx.x; rb < nrb && !aborted(bs); rb += gridDim.x, ++rbi) {
+      for (int w = blockIdx.x; w < items && !aborted(bs); w += gridDim.x, ++rbi) {
+        const int cs = w % ncs;
+        const int t0 = cs * per_slice, t1 = min(ntiles, t0 + per_slice);
         if (!tc::mbar_wait(&bs->afull, rbi & 1, kSpin)) {
           raise_abort(bs, status);
           break;
         }
-        for (int t = 0; t < ntiles; ++t, ++used, ++accu) {
+        for (int t = t0; t < t1; ++t, ++used, ++accu) {
           const int s = int(used % kStages);
           const int b = int(accu & 1);
           if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kStages) & 1, kSpin) ||
@@ -277,10 +324,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc::fence_after_sync();
-          const uint32_t bbase = tc::smem_u32(sB + s * kBTile);
-          const uint32_t d = tmem + uint32_t(b * kTN);
-          for (int ks = 0; ks < ksteps; ++ks)
-            tc::mma_bf16(d, tc::sdesc_k128(abase + ks * 32), tc::sdesc_k128(bbase + ks * 32), idesc, ks > 0);
+          const uint32_t bh = tc::smem_u32(sB + s * S::kPlanes * S::kBTile), bl = bh + S::kBTile;
+          const uint32_t d = tmem + uint32_t(b * TN);
+          for (int ks = 0; ks < ksteps; ++ks) {
+            tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, ks > 0);
+            if (NP == 3) {
+              tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bl + ks * 32), idesc, 1u);
+              tc::mma_bf16(d, tc::sdesc_k128(al + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, 1u);
+            }
+          }
           tc::mma_commit(&bs->empty[s]);
           tc::mma_commit(&bs->accf[b]);
         }
@@ -293,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue ----------------
     const int ew = warp - 2;
-    const int half = ew >> 2;  // 128-column half of the tile
+    const int half = ew >> 2;  // half of the tile's columns
     const int q = warp & 3;    // TMEM lane quarter this warp may access
     const int row_local = q * 32 + lane;
     const int L = half * kTM + row_local;
@@ -305,15 +357,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const volatile unsigned long long* partner = pubs + (1 - half) * kTM + row_local;
     uint32_t* slot = stash + (ew * 32 + lane) * kSlot;
     long long accu = 0;
-    for (int rb = blockIdx.x; rb < nrb; rb += gridDim.x) {
+    for (int w = blockIdx.x; w < items; w += gridDim.x) {
       if (__any_sync(kFull, aborted(bs))) break;
-      const int i = rb * kTM + row_local;
-      const unsigned tag = unsigned(rb);
+      const int rb = w / ncs, cs = w - rb * ncs;
+      const int t0 = cs * per_slice, t1 = min(ntiles, t0 + per_slice);
+      const int p = rb * kTM + row_local;                      // row of A
+      const int self = p < m ? (rows ? rows[p] : p) : -1;     // its column in Psi
+      const int64_t out = int64_t(cs) * m + p;                 // its list pair
+      const unsigned tag = unsigned(w);
       ListState st{0, 0, -1.f};
       bool parked = false;  // this lane's stash slot holds a chunk
       int sj = 0;           // its first column
       bool ok = true;
-      for (int t = 0; t < ntiles; ++t, ++accu) {
+      for (int t = t0; t < t1; ++t, ++accu) {
         const int b = int(accu & 1);
         ok = __all_sync(kFull, tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin));
         if (!ok) {
@@ -321,21 +377,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc::fence_after_sync();
-        const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * kTN + half * 128);
-        const int j0 = t * kTN + half * 128;
-        // the whole 128-column slice in one round trip, then hand the
-        // accumulator back to the MMA warp before scanning
-        uint32_t r[4][32];
+        const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * TN + half * (TN / 2));
+        const int j0 = t * TN + half * (TN / 2);
+        // the half's columns in one round trip, then hand the accumulator
+        // back to the MMA warp before scanning
+        uint32_t r[S::kChunks][32];
         __syncwarp();
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
+        for (int c = 0; c < S::kChunks; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
         tc::tmem_ld_wait();
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
-        float thr = fmaxf(st.minv, partner_min(partner, tag));
+        const float thr = fmaxf(st.minv, partner_min(partner, tag));
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < S::kChunks; ++c) {
           float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // four short max chains
 #pragma unroll
           for (int e = 0; e < 32; e += 4) {
@@ -345,43 +401,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             m3 = fmaxf(m3, fabsf(__uint_as_float(r[c][e + 3])));
           }
           if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr) {
-            if (!parked) {
+            if (STASH && !parked) {
 #pragma unroll
               for (int k = 0; k < 8; ++k)
                 reinterpret_cast<uint4*>(slot)[k] = make_uint4(r[c][4 * k], r[c][4 * k + 1], r[c][4 * k + 2], r[c][4 * k + 3]);
               parked = true;
               sj = j0 + c * 32;
             } else {
-              uint32_t mask = 0;
-#pragma unroll
-              for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(r[c][e])) > thr ? 1u : 0u) << e;
-              while (mask) {
-                const int e = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const float v = fabsf(__uint_as_float(pick32(r[c], e)));
-                const int j = j0 + c * 32 + e;
-                if (v > thr && j < n && j != i) {
-                  st = offer(mlv, mli, msv, msp, mine, tag, st, v, j);
-                  thr = fmaxf(st.minv, partner_min(partner, tag));
-                }
-              }
+              st = insert_chunk(r[c], j0 + c * 32, self, n, mlv, mli, msv, msp, mine, partner, tag, st);
             }
           }
         }
-        if (__popc(__ballot_sync(kFull, parked)) >= kBatch) {
-          if (parked) st = drain(slot, sj, i, n, mlv, mli, msv, msp, mine, partner, tag, st);
+        if (STASH && __popc(__ballot_sync(kFull, parked)) >= kBatch) {
+          if (parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st);
           parked = false;
           __syncwarp();
         }
       }
       if (!ok || __any_sync(kFull, aborted(bs))) break;
-      if (parked) st = drain(slot, sj, i, n, mlv, mli, msv, msp, mine, partner, tag, st);
-      if (i < n) {
+      if (STASH && parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st);
+      if (p < m) {
         for (int c = 0; c < kC; ++c) {
-          cand_idx[int64_t(i) * (2 * kC) + half * kC + c] = c < st.cnt ? mli[c * kLists] : -1;
-          cand_val[int64_t(i) * (2 * kC) + half * kC + c] = c < st.cnt ? mlv[c * kLists] : -1.f;
+          cand_idx[out * (2 * kC) + half * kC + c] = c < st.cnt ? mli[c * kLists] : -1;
+          cand_val[out * (2 * kC) + half * kC + c] = c < st.cnt ? mlv[c * kLists] : -1.f;
         }
-        thr_out[int64_t(i) * 2 + half] = st.minv;  // -1 while the list was never full
+        thr_out[out * 2 + half] = st.minv;  // -1 while the list was never full
       }
       __syncwarp();
     }
@@ -389,21 +433,50 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 512);
+    tc::tmem_dealloc(tmem, S::kTmemCols);
   }
 }
 
-// bf16 operands of the screen: A = bf16(V psi), B = bf16(V), n x 64, K zero-padded.
+// Operands of the screens, rows x 64 bf16 row-major, K zero-padded.
+__device__ __forceinline__ double vload(const void* V, int v64, int64_t idx) {
+  return v64 ? static_cast<const double*>(V)[idx] : double(static_cast<const float*>(V)[idx]);
+}
+
+// Main screen: A = bf16(V psi), B = bf16(V).
 __global__ void prep_tc_kernel(const void* V, int v64, int64_t ldv, const double* __restrict__ psi, int64_t n, int r,
                                __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B) {
   const int64_t total = n * kKP;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t i = e / kKP;
     const int k = int(e - i * kKP);
-    double v = 0.0;
-    if (k < r) v = v64 ? static_cast<const double*>(V)[i * ldv + k] : double(static_cast<const float*>(V)[i * ldv + k]);
+    const double v = k < r ? vload(V, v64, i * ldv + k) : 0.0;
     A[e] = __float2bfloat16_rn(k < r ? float(v * psi[k]) : 0.f);
     B[e] = __float2bfloat16_rn(float(v));
+  }
+}
+
+// Repair screen, split planes x = hi + lo (hi = bf16(x), lo = bf16(x - hi)):
+// A for the listed rows (x = V_ik psi_k), and lo of B (x = V_ik; hi is the
+// main screen's B).
+__global__ void prep_split_kernel(const void* V, int v64, int64_t ldv, const double* __restrict__ psi, int64_t n, int r,
+                                  const int* __restrict__ rows, int64_t m, const __nv_bfloat16* __restrict__ Bh,
+                                  __nv_bfloat16* __restrict__ Bl, __nv_bfloat16* __restrict__ Ah,
+                                  __nv_bfloat16* __restrict__ Al) {
+  const int64_t nb = n * kKP, total = nb + m * kKP;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    if (e < nb) {
+      const int64_t i = e / kKP;
+      const int k = int(e - i * kKP);
+      const float x = k < r ? float(vload(V, v64, i * ldv + k)) : 0.f;
+      Bl[e] = __float2bfloat16_rn(x - __bfloat162float(Bh[e]));
+    } else {
+      const int64_t f = e - nb, p = f / kKP;
+      const int k = int(f - p * kKP);
+      const double x = k < r ? vload(V, v64, int64_t(rows[p]) * ldv + k) * psi[k] : 0.0;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(float(x));
+      Ah[f] = hi;
+      Al[f] = __float2bfloat16_rn(float(x - double(__bfloat162float(hi))));
+    }
   }
 }
 
@@ -424,23 +497,56 @@ EncodeTiledFn encode_fn() {
 }
 
 // rows x 64 bf16, row-major; box boxrows x 64 (one 128-byte swizzle span)
-bool make_map(CUtensorMap* m, void* base, int64_t rows, int boxrows) {
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int boxrows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {cuuint64_t(kKP), cuuint64_t(rows)};
   cuuint64_t strides[1] = {cuuint64_t(kKP) * 2};
   cuuint32_t box[2] = {cuuint32_t(kKP), cuuint32_t(boxrows)};
   cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+template <int TN, int NP, bool STASH>
+cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, const void* bh, const void* bl, int n,
+                       int ncs, const int* rows, int r, int32_t* cidx, float* cval, float* thr) {
+  CUtensorMap mah, mal, mbh, mbl;
+  if (!make_map(&mah, ah, m, kTM) || !make_map(&mbh, bh, n, TN)) return cudaErrorInvalidValue;
+  mal = mah;
+  mbl = mbh;
+  if (NP == 3 && (!make_map(&mal, al, m, kTM) || !make_map(&mbl, bl, n, TN))) return cudaErrorInvalidValue;
+  auto kern = screen_tc_kernel<TN, NP, STASH>;
+  const size_t smem = smem_bytes<Screen<TN, NP, STASH>>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int items = int((m + kTM - 1) / kTM) * ncs;
+  const int grid = std::min(items, h->num_sms);
+  kern<<<grid, kThreads, smem, h->stream>>>(mah, mal, mbh, mbl, m, n, ncs, rows, (r + 15) / 16, cidx, cval, thr,
+                                            h->d_status);
+  return cudaGetLastError();
+}
+
+// main: TN 256, one product, stash; repair: TN 128, split products
+using MainScreen = Screen<256, 1, true>;
+using RepairScreen = Screen<128, 3, false>;
+static_assert(smem_bytes<MainScreen>() <= 232448 && smem_bytes<RepairScreen>() <= 232448, "shared memory");
 
 }  // namespace
 
 size_t topk_tc_scratch_bytes(int64_t d, int r, gmgm_prec prec) {
   if (prec != GMGM_BF16) return 0;
-  return Carve::round(size_t(d) * kKP * 2) * 2 + 1024;
+  // main A, B; repair lo of B, hi and lo of A (at most d listed rows)
+  return Carve::round(size_t(d) * kKP * 2) * 5 + 1024;
+}
+
+int screen_tc_slices(int64_t m, int num_sms, int64_t cap_rows) {
+  const int64_t nrb = (m + kTM - 1) / kTM;
+  int64_t ncs = std::max<int64_t>(1, num_sms / std::max<int64_t>(1, nrb));
+  ncs = std::min<int64_t>(ncs, 8);
+  ncs = std::min<int64_t>(ncs, std::max<int64_t>(1, cap_rows / std::max<int64_t>(1, m)));
+  return int(ncs);
 }
 
 cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi,
@@ -454,16 +560,27 @@ cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, in
     const unsigned blocks = unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 16));
     prep_tc_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, A, B);
   }
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, A, d, kTM) || !make_map(&mb, B, d, kTN)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(screen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
-  if (e != cudaSuccess) return e;
-  const int nrb = int((d + kTM - 1) / kTM);
-  const int grid = std::min(nrb, h->num_sms);
-  const int ksteps = (r + 15) / 16;
-  screen_tc_kernel<<<grid, kThreads, kSmemBytes, h->stream>>>(ma, mb, int(d), ksteps, cidx, cval, thr, h->d_status);
   note_launch(2);
-  return cudaGetLastError();
+  return run_screen<256, 1, true>(h, A, nullptr, int(d), B, nullptr, int(d), 1, nullptr, r, cidx, cval, thr);
+}
+
+cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,
+                                    const double* psi, const int* rows, int m, int ncs, int32_t* cidx, float* cval,
+                                    float* thr, void* scratch) {
+  if (r > kKP || d > (int64_t(1) << 30) || m < 1) return cudaErrorNotSupported;
+  Carve c(scratch);
+  c.take<__nv_bfloat16>(size_t(d) * kKP);  // main A (not used here)
+  const __nv_bfloat16* Bh = c.take<__nv_bfloat16>(size_t(d) * kKP);
+  __nv_bfloat16* Bl = c.take<__nv_bfloat16>(size_t(d) * kKP);
+  __nv_bfloat16* Ah = c.take<__nv_bfloat16>(size_t(d) * kKP);
+  __nv_bfloat16* Al = c.take<__nv_bfloat16>(size_t(d) * kKP);
+  {
+    const int64_t total = (d + m) * kKP;
+    const unsigned blocks = unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 16));
+    prep_split_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, rows, m, Bh, Bl, Ah, Al);
+  }
+  note_launch(2);
+  return run_screen<128, 3, false>(h, Ah, Al, m, Bh, Bl, int(d), ncs, rows, r, cidx, cval, thr);
 }
 
 }  // namespace gmgm

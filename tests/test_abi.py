@@ -52,17 +52,18 @@ def test_struct_layouts_match_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "gmgm.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(gmgm_matrix), sizeof(gmgm_problem), sizeof(gmgm_solve_opts),"
-        "sizeof(gmgm_solve_stats), sizeof(gmgm_topk_stats),"
+        "sizeof(gmgm_solve_stats), sizeof(gmgm_topk_stats), sizeof(gmgm_train_opts),"
         "offsetof(gmgm_problem, E), offsetof(gmgm_problem, n_modalities),"
-        "offsetof(gmgm_problem, mod_axes));return 0;}\n")
+        "offsetof(gmgm_problem, mod_axes), offsetof(gmgm_train_opts, seed));return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(_lib.Matrix), ctypes.sizeof(_lib.Problem), ctypes.sizeof(_lib.SolveOpts),
-            ctypes.sizeof(_lib.SolveStats), ctypes.sizeof(_lib.TopkStats),
-            _lib.Problem.E.offset, _lib.Problem.n_modalities.offset, _lib.Problem.mod_axes.offset]
+            ctypes.sizeof(_lib.SolveStats), ctypes.sizeof(_lib.TopkStats), ctypes.sizeof(_lib.TrainOpts),
+            _lib.Problem.E.offset, _lib.Problem.n_modalities.offset, _lib.Problem.mod_axes.offset,
+            _lib.TrainOpts.seed.offset]
     assert got == want
 
 

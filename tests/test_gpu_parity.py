@@ -290,6 +290,25 @@ def test_topk_identity_all_zero_ties(g, cuda_dev):
     assert st["rows_uncertified"] == 40
 
 
+def test_topk_bf16_repair_screen_certifies_near_ties(g, cuda_dev):
+    # clustered rows (30 centroids + 2e-3 noise): neighbours inside a cluster
+    # differ by far less than the BF16 screen's error bound, so most rows fail
+    # its certification; the 3xBF16 repair screen (bound ~120x tighter)
+    # certifies them, and the result is the exact FP64 top-k
+    rng = _rng(31)
+    d, r, k = 4000, 50, 10
+    cent = rng.standard_normal((30, r))
+    V = (cent[rng.integers(0, 30, d)] + 2e-3 * rng.standard_normal((d, r))).astype(np.float32)
+    lam = rng.uniform(0.5, 2.0, r)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(lam).to(cuda_dev), k,
+                                  prec=g.BF16)
+    frac = _check_topk(V.astype(np.float64), lam, k, idx.cpu().numpy(), val.cpu().numpy())
+    assert frac > 0.5
+    assert st["screen_err_ratio"] <= 1.0, st
+    assert st["rows_uncertified"] > d // 4, st
+    assert st["rows_exact"] <= st["rows_uncertified"] // 4, st
+
+
 def test_topk_argument_errors(g, cuda_dev):
     V = torch.zeros(10, 3, device=cuda_dev)
     psi = torch.ones(3, dtype=torch.float64, device=cuda_dev)
@@ -297,6 +316,11 @@ def test_topk_argument_errors(g, cuda_dev):
         g.topk_network(V, psi, 10)      # k >= d
     with pytest.raises(g.GmgmError):
         g.topk_network(V, psi, 33)      # k > 32
+    with pytest.raises(g.GmgmError):
+        g.topk_network(V, psi, 3, g.BF16X3)  # no split-product screen
+    with pytest.raises(g.GmgmError):
+        g.topk_network(torch.zeros(100, 65, device=cuda_dev), torch.ones(65, dtype=torch.float64, device=cuda_dev),
+                       3, g.BF16)       # tensor-core screen needs r <= 64
 
 
 # ---- whole two-axis fit ---------------------------------------------------------------

@@ -3,7 +3,7 @@
 import numpy as np
 import pytest
 
-from oracle.gram import gram, gram_multimodal, log1p_centre, matricize
+from oracle.gram import gram, gram_multimodal, log1p_centre, log1p_col_means, matricize
 from oracle.spectra import dual_lift, top_eigh, two_axis_spectra
 from synth import planted_c1
 
@@ -57,6 +57,21 @@ def test_log1p_centre():
     np.testing.assert_allclose(x.mean(axis=0), 0, atol=1e-15)
     raw = np.log(1 + c)
     np.testing.assert_allclose(x + raw.mean(axis=0), raw, rtol=1e-15)
+
+
+def test_log1p_col_means_closed_forms_and_row_blocks():
+    # column 0 constant 4 -> log 5; column 1 one 1 in every 4 rows -> log(2)/4;
+    # column 2 the counts 0..n-1 -> log(n!)/n (Python's lgamma), any blocking
+    import math
+    n = 1000
+    c = np.zeros((n, 3), dtype=np.float32)
+    c[:, 0] = 4
+    c[::4, 1] = 1
+    c[:, 2] = np.arange(n)
+    want = [math.log(5.0), math.log(2.0) / 4, math.lgamma(n + 1) / n]
+    for size in (n, 1, 7, 256):
+        got = log1p_col_means((c[i:i + size] for i in range(0, n, size)), threads=3)
+        np.testing.assert_allclose(got, want, rtol=1e-13)
 
 
 def test_top_eigh_invariants():
