@@ -6,7 +6,8 @@
 // product); plain BF16 forms hi.hi^T only.
 //
 // Work item = (output tile 128 genes x 256 genes of the upper triangle,
-// K range of the cells).  The tensor core's FP32 accumulation is kept short:
+// K split: every nsplit-th drain block of the cells, so all CTAs sweep the
+// cells together and share each slice of the planes through L2).  The tensor core's FP32 accumulation is kept short:
 // the accumulator is drained every kSub K blocks (1024 cells) into an FP64
 // running tile owned by the CTA.  Its rounding error grows with the length
 // of a block (measured at 1M cells x 2000 genes against an FP64 Gram of the
@@ -18,7 +19,7 @@
 //   warp 1      MMA issuer: tcgen05.mma M=128 N=256 K=16, FP32 accumulator
 //               in TMEM (double-buffered, 2 x 256 columns);
 //   warps 2-5   epilogue: tcgen05.ld each drained accumulator and add it to
-//               the item's FP64 tile; a second kernel sums the K ranges in
+//               the item's FP64 tile; a second kernel sums the K splits in
 //               FP64 and writes both triangles of S.
 // Every wait is bounded (GMGM_DEV_TIMEOUT on expiry, TMEM freed on exit).
 #include <cuda.h>
@@ -85,8 +86,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = bs->tmem_base;
+  // item w = (K split ch, tile ti); split ch takes the drain blocks ch,
+  // ch + nsplit, ... so every CTA sweeps the cells in the same order and the
+  // current slice of the X^T planes is read from L2 by all tiles
   const int items = ntiles * nsplit;
-  const int kb_per = (nkb_total + nsplit - 1) / nsplit;
+  const int kstride = nsplit * kSub;
   const uint32_t stage_tx = uint32_t(nprod == 3 ? kStageBytes : kABytes + kBBytes);
 
   if (warp == 0) {
@@ -95,21 +99,23 @@ __global__ void __launch_bounds__(kGThreads, 1)
       for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
         const int ch = w / ntiles, ti = w - ch * ntiles;
         const int2 tl = tiles[ti];
-        const int kb0 = ch * kb_per, kb1 = min(nkb_total, kb0 + kb_per);
-        for (int kb = kb0; kb < kb1; ++kb, ++issued) {
-          const int s = int(issued % kGStages);
-          const uint32_t k = uint32_t(issued / kGStages);
-          if (!tc::mbar_wait(&bs->empty[s], (k & 1) ^ 1, kGSpin)) {
-            g_abort(bs, status);
-            break;
-          }
-          uint8_t* st = smem + s * kStageBytes;
-          tc::mbar_arrive_expect_tx(&bs->full[s], stage_tx);
-          tc::tma_load_2d(st, &tAh, &bs->full[s], kb * 64, tl.x * kGM);
-          tc::tma_load_2d(st + 2 * kABytes, &tBh, &bs->full[s], kb * 64, tl.y * kGN);
-          if (nprod == 3) {
-            tc::tma_load_2d(st + kABytes, &tAl, &bs->full[s], kb * 64, tl.x * kGM);
-            tc::tma_load_2d(st + 2 * kABytes + kBBytes, &tBl, &bs->full[s], kb * 64, tl.y * kGN);
+        for (int sb = ch * kSub; sb < nkb_total && !g_aborted(bs); sb += kstride) {
+          const int se = min(nkb_total, sb + kSub);
+          for (int kb = sb; kb < se; ++kb, ++issued) {
+            const int s = int(issued % kGStages);
+            const uint32_t k = uint32_t(issued / kGStages);
+            if (!tc::mbar_wait(&bs->empty[s], (k & 1) ^ 1, kGSpin)) {
+              g_abort(bs, status);
+              break;
+            }
+            uint8_t* st = smem + s * kStageBytes;
+            tc::mbar_arrive_expect_tx(&bs->full[s], stage_tx);
+            tc::tma_load_2d(st, &tAh, &bs->full[s], kb * 64, tl.x * kGM);
+            tc::tma_load_2d(st + 2 * kABytes, &tBh, &bs->full[s], kb * 64, tl.y * kGN);
+            if (nprod == 3) {
+              tc::tma_load_2d(st + kABytes, &tAl, &bs->full[s], kb * 64, tl.x * kGM);
+              tc::tma_load_2d(st + 2 * kABytes + kBBytes, &tBl, &bs->full[s], kb * 64, tl.y * kGN);
+            }
           }
         }
       }
@@ -123,8 +129,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       long long used = 0, accu = 0;
       for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
         const int ch = w / ntiles;
-        const int kb0 = ch * kb_per, kb1 = min(nkb_total, kb0 + kb_per);
-        for (int sb = kb0; sb < kb1 && !g_aborted(bs); sb += kSub, ++accu) {
+        for (int sb = ch * kSub; sb < nkb_total && !g_aborted(bs); sb += kstride, ++accu) {
           const int b = int(accu & 1);
           if (!tc::mbar_wait(&bs->acce[b], (uint32_t(accu >> 1) & 1) ^ 1, kGSpin)) {
             g_abort(bs, status);
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
           tc::fence_after_sync();
           const uint32_t d = tmem + uint32_t(b * kGN);
           bool first = true;
-          const int se = min(kb1, sb + kSub);
+          const int se = min(nkb_total, sb + kSub);
           for (int kb = sb; kb < se; ++kb, ++used) {
             const int s = int(used % kGStages);
             if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kGStages) & 1, kGSpin)) {
@@ -168,9 +173,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     long long accu = 0;
     for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
       const int ch = w / ntiles;
-      const int kb0 = ch * kb_per, kb1 = min(nkb_total, kb0 + kb_per);
       double2* dst = reinterpret_cast<double2*>(part + (int64_t(w) * kGM + row) * kGN);
-      for (int sb = kb0; sb < kb1 && !g_aborted(bs); sb += kSub, ++accu) {
+      for (int sb = ch * kSub; sb < nkb_total && !g_aborted(bs); sb += kstride, ++accu) {
         const int b = int(accu & 1);
         if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kGSpin)) {
           g_abort(bs, status);
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
         tc::fence_after_sync();
         const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * kGN);
-        const bool init = sb == kb0;
+        const bool init = sb == ch * kSub;
 #pragma unroll 1
         for (int c = 0; c < kGN / 32; ++c) {
           uint32_t r[32];
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   }
 }
 
-// S[a][c] = sum over K ranges of the partial tile holding (min, max) (FP64).
+// S[a][c] = sum over K splits of the partial tile holding (min, max) (FP64).
 __global__ void gram_tc_combine_kernel(const double* __restrict__ part, const int* __restrict__ tile_of, int ntn,
                                        int ntiles, int nsplit, int64_t p, double* __restrict__ S, int64_t lds,
                                        int accumulate) {
@@ -270,7 +274,7 @@ GramPlan plan(const gmgm_matrix* m, int num_sms) {
     for (int mt = 0; mt < g.ntm; ++mt)
       if (int64_t(nt) * kGN + kGN - 1 >= int64_t(mt) * kGM) ++g.ntiles;
   g.nkb = int(m->ld_t / 64);
-  // K ranges per tile: enough work items to cover the SMs, each range at
+  // K splits per tile: enough work items to cover the SMs, each split at
   // least one drain long
   g.nsplit = std::max(1, std::min((num_sms + g.ntiles / 2) / g.ntiles, (g.nkb + kSub - 1) / kSub));
   return g;
