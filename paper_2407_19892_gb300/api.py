@@ -280,3 +280,102 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
     ir, vr, sr = topk_network(v_rows, lam_rows, k_rows, topk_prec, h=h)
     ic, vc, sc = topk_network(v_cols, lam_cols, k_cols, L.FP32, h=h)
     return TwoAxisResult(e_rows, v_rows, e_cols, v_cols, lam_rows, lam_cols, ir, vr, ic, vc, st, sr, sc)
+
+
+# ---- several modalities sharing the cell axis; one K-axis tensor ---------------
+
+@dataclass
+class MultiAxisResult:
+    E: list        # per axis, FP64 descending
+    V: list        # per axis, eigenvectors as columns (cells: FP32 lift; others FP64)
+    lam: list      # per axis, FP64
+    idx: list      # per axis, int32 [d_l, k_l] (None where no network was asked)
+    val: list      # per axis, FP32 [d_l, k_l]
+    solve: dict = field(default_factory=dict)
+    topk_stats: list = field(default_factory=list)
+
+
+def fit_multimodal(counts, r_cells: int, ks, gram_prec: int = L.BF16X3, topk_prec: int = L.BF16,
+                   tol: float = 1e-9, h: Handle = None) -> MultiAxisResult:
+    """Count matrices (cells x p_m, FP32, on the GPU) sharing the cell axis.
+
+    Section "Algorithm": the Gram of an axis shared by several modalities is
+    the Gram of their concatenation.  Each modality is preprocessed into its
+    column slice of one X = [X_1 X_2 ...] (and its rows of the BF16 planes of
+    X^T); one column Gram of X holds every block.  The cell axis takes the top
+    r_cells eigenpairs of that Gram lifted through X; modality m's own axis
+    takes the full spectrum of its diagonal block.  The solve couples
+    (cells, m) for every modality; one network per axis (ks: k per axis,
+    cells first)."""
+    dev = counts[0].device
+    h = h or handle(dev)
+    n = counts[0].shape[0]
+    ps = [c.shape[1] for c in counts]
+    P = sum(ps)
+    for c in counts:
+        _need_cuda(c, torch.float32, "counts")
+        if c.dim() != 2 or c.shape[0] != n or c.stride(1) != 1:
+            raise ValueError("every count matrix must be row-major cells x features with the same cells")
+    split = gram_prec != L.FP32
+    x = torch.empty(n, P, dtype=torch.float32, device=dev)
+    ld_t = ((n + 63) // 64) * 64 if split else 0
+    hi = torch.empty(P, ld_t, dtype=torch.bfloat16, device=dev) if split else None
+    lo = torch.empty(P, ld_t, dtype=torch.bfloat16, device=dev) if split else None
+    off = 0
+    for c, p in zip(counts, ps):
+        h.check(h.lib.gmgm_preprocess(h.h, n, p, _ptr(c), c.stride(0), _ptr(x[:, off:]), x.stride(0),
+                                      _ptr(hi[off:]) if split else None, _ptr(lo[off:]) if split else None,
+                                      ld_t, None))
+        off += p
+    S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
+    e_c, W_c = spectra(S, r_cells, True, h=h)
+    E, V = [e_c], [lift(x, W_c, e_c, r_cells, h=h)]
+    off = 0
+    for p in ps:
+        e, W = spectra(S[off:off + p, off:off + p], p, True, h=h)
+        E.append(e)
+        V.append(W)
+        off += p
+    lams, st = eigsolve(E, [(0, m + 1) for m in range(len(ps))], tol=tol, h=h)
+    idx, val, sts = [], [], []
+    for a in range(len(E)):
+        if ks[a]:
+            i, v, t = topk_network(V[a], lams[a], ks[a], topk_prec if a == 0 else L.FP32, h=h)
+        else:
+            i = v = t = None
+        idx.append(i)
+        val.append(v)
+        sts.append(t)
+    return MultiAxisResult(E, V, lams, idx, val, st, sts)
+
+
+def fit_tensor(t: torch.Tensor, ks, tol: float = 1e-9, h: Handle = None) -> MultiAxisResult:
+    """One 3-axis tensor T (d0 x d1 x d2, FP32, row-major, on the GPU): the
+    Gram of every axis (Notation: S_l = mat_l[T] mat_l[T]^T), its full FP64
+    spectrum, the solve over one modality of all three axes, and one network
+    per axis (ks: k per axis, None for none)."""
+    h = h or handle(t.device)
+    _need_cuda(t, torch.float32, "t")
+    if t.dim() != 3:
+        raise ValueError("t must be a 3-axis tensor")
+    t = t.contiguous()
+    d0, d1, d2 = t.shape
+    Ss = [gram(t.reshape(d0, d1 * d2), L.SIDE_ROWS, L.FP32, h=h),
+          gram(t, L.SIDE_ROWS, L.FP32, h=h),
+          gram(t.reshape(d0 * d1, d2), L.SIDE_COLS, L.FP32, h=h)]
+    E, V = [], []
+    for S in Ss:
+        e, W = spectra(S, S.shape[0], True, h=h)
+        E.append(e)
+        V.append(W)
+    lams, st = eigsolve(E, [(0, 1, 2)], tol=tol, h=h)
+    idx, val, sts = [], [], []
+    for a in range(3):
+        if ks[a]:
+            i, v, s_ = topk_network(V[a], lams[a], ks[a], L.FP32, h=h)
+        else:
+            i = v = s_ = None
+        idx.append(i)
+        val.append(v)
+        sts.append(s_)
+    return MultiAxisResult(E, V, lams, idx, val, st, sts)
