@@ -289,7 +289,7 @@ def main():
         ev[5].record(stream)
         g.topk_network(U, lr, a.k_cells, topk_prec, h=h)
         ev[6].record(stream)
-        g.topk_network(W, lc, a.k_genes, g.FP32, h=h)
+        g.topk_network(W, lc, a.k_genes, g.FP32, ortho=True, h=h)
         ev[7].record(stream)
         torch.cuda.synchronize()
         out = {n: round(ev[i].elapsed_time(ev[i + 1]), 3) for i, n in enumerate(names)}

@@ -360,6 +360,16 @@ typedef struct {
  *   k       1 <= k <= 32 and k < d.
  *   prec    screen arithmetic: GMGM_FP32 (SIMT) or GMGM_BF16 (tcgen05 tensor
  *           cores, r <= 64); any other value is GMGM_E_ARG.
+ *   flags   0, or GMGM_TOPK_ORTHO: V is square (r == d) with orthonormal
+ *           columns (the full eigenvector matrix of an axis at full rank).
+ *           Then Psi = c I + V diag(psi - c) V^T with c = min psi, and the
+ *           off-diagonal entries depend only on the columns with psi > c
+ *           (the identifiability appendix's diagonal shift, exact when
+ *           V V^T = I): the network is computed from those columns alone,
+ *           and when there are none every off-diagonal entry is 0 (each row
+ *           takes the k lowest columns j != i by the tie rule, values 0).
+ *           The caller guarantees the orthonormality; it is not checked.
+ *           With r - (columns dropped) > 64 a BF16 request screens in FP32.
  *   idx_out device, d x k int32: column indices, by |Psi_ij| descending.
  *   val_out device, d x k FP32: the signed Psi_ij, computed in FP64 from V
  *           (as given) and psi, then rounded.
@@ -369,10 +379,12 @@ typedef struct {
  * screened value plus the bound); rows that fail are recomputed in FP64, so
  * idx_out is the exact FP64 top-k of the given V and psi.
  * Errors: GMGM_E_ARG. */
+#define GMGM_TOPK_ORTHO 1u
+
 int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r,
                       const void* V, int v_fp64, int64_t ldv,
                       const double* psi, int32_t k, gmgm_prec prec,
-                      int32_t* idx_out, float* val_out,
+                      uint32_t flags, int32_t* idx_out, float* val_out,
                       gmgm_topk_stats* stats);
 
 #ifdef __cplusplus

@@ -56,6 +56,7 @@ class TrainOpts(ctypes.Structure):
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
+TOPK_ORTHO = 1
 MLP_IN, MLP_HIDDEN, MLP_OUT = 132, 256, 128
 MLP_PARAMS = 256 * 132 + 256 + 256 * 256 + 256 + 128 * 256 + 128
 
@@ -96,7 +97,7 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_float)]),
     "gmgm_warmstart_infer": (c_int, [c_vp, c_vp, c_vp, c_i32, c_vp, c_i32, c_dbl, c_vp, c_vp]),
     "gmgm_topk_network": (c_int, [c_vp, c_i64, c_i32, c_vp, c_int, c_i64, c_vp, c_i32, c_int,
-                                  c_vp, c_vp, ctypes.POINTER(TopkStats)]),
+                                  ctypes.c_uint32, c_vp, c_vp, ctypes.POINTER(TopkStats)]),
 }
 
 _lib = None

@@ -217,8 +217,10 @@ def eigsolve(E, modalities=None, eps=None, init=None, tol=1e-9, max_newton=200, 
 
 # ---- top-k network -------------------------------------------------------------
 
-def topk_network(V: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32, h: Handle = None):
-    """Per-row top-k of |V diag(psi) V^T| (diagonal excluded).  Returns
+def topk_network(V: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32, ortho: bool = False,
+                 h: Handle = None):
+    """Per-row top-k of |V diag(psi) V^T| (diagonal excluded).  ortho: V is
+    square with orthonormal columns (GMGM_TOPK_ORTHO).  Returns
     (idx int32 [d, k], val float32 [d, k], stats dict)."""
     h = h or handle(V.device)
     if V.dtype not in (torch.float32, torch.float64) or not V.is_cuda:
@@ -231,8 +233,8 @@ def topk_network(V: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32,
     val = torch.empty(d, k, dtype=torch.float32, device=V.device)
     st = L.TopkStats()
     h.check(h.lib.gmgm_topk_network(h.h, d, r, _ptr(V), int(V.dtype == torch.float64), V.stride(0),
-                                    _ptr(psi.contiguous()), k, prec, _ptr(idx), _ptr(val),
-                                    ctypes.byref(st)))
+                                    _ptr(psi.contiguous()), k, prec, L.TOPK_ORTHO if ortho else 0, _ptr(idx),
+                                    _ptr(val), ctypes.byref(st)))
     return idx, val, st.as_dict()
 
 
@@ -278,7 +280,8 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
     (lam_rows, lam_cols), st = eigsolve([e_rows, e_cols], [(0, 1)], tol=tol, fp32_phase=fp32_phase,
                                         init=init, h=h)
     ir, vr, sr = topk_network(v_rows, lam_rows, k_rows, topk_prec, h=h)
-    ic, vc, sc = topk_network(v_cols, lam_cols, k_cols, L.FP32, h=h)
+    # the gene axis at full rank: V = W is square and orthonormal
+    ic, vc, sc = topk_network(v_cols, lam_cols, k_cols, L.FP32, ortho=v_cols.shape[0] == v_cols.shape[1], h=h)
     return TwoAxisResult(e_rows, v_rows, e_cols, v_cols, lam_rows, lam_cols, ir, vr, ic, vc, st, sr, sc)
 
 
@@ -340,7 +343,8 @@ def fit_multimodal(counts, r_cells: int, ks, gram_prec: int = L.BF16X3, topk_pre
     idx, val, sts = [], [], []
     for a in range(len(E)):
         if ks[a]:
-            i, v, t = topk_network(V[a], lams[a], ks[a], topk_prec if a == 0 else L.FP32, h=h)
+            # feature axes at full rank: square orthonormal W
+            i, v, t = topk_network(V[a], lams[a], ks[a], topk_prec if a == 0 else L.FP32, ortho=a > 0, h=h)
         else:
             i = v = t = None
         idx.append(i)
@@ -372,7 +376,7 @@ def fit_tensor(t: torch.Tensor, ks, tol: float = 1e-9, h: Handle = None) -> Mult
     idx, val, sts = [], [], []
     for a in range(3):
         if ks[a]:
-            i, v, s_ = topk_network(V[a], lams[a], ks[a], L.FP32, h=h)
+            i, v, s_ = topk_network(V[a], lams[a], ks[a], L.FP32, ortho=True, h=h)
         else:
             i = v = s_ = None
         idx.append(i)

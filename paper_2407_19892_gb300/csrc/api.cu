@@ -345,7 +345,7 @@ int gmgm_warmstart_infer(gmgm_handle* h, const float* params, const double* E0, 
 }
 
 int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64,
-                      int64_t ldv, const double* psi, int32_t k, gmgm_prec prec,
+                      int64_t ldv, const double* psi, int32_t k, gmgm_prec prec, uint32_t flags,
                       int32_t* idx_out, float* val_out, gmgm_topk_stats* stats) {
   if (!h) return GMGM_E_ARG;
   if (d < 2 || r < 1 || !V || !psi || !idx_out || !val_out || ldv < r)
@@ -355,9 +355,17 @@ int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v
   if (r > 4096) return fail(h, GMGM_E_ARG, "gmgm_topk_network: r > 4096");
   if (prec != GMGM_FP32 && prec != GMGM_BF16)
     return fail(h, GMGM_E_ARG, "gmgm_topk_network: prec must be FP32 or BF16");
-  if (prec != GMGM_FP32 && r > 64)
+  if (flags & ~GMGM_TOPK_ORTHO) return fail(h, GMGM_E_ARG, "gmgm_topk_network: unknown flags");
+  if ((flags & GMGM_TOPK_ORTHO) && r != d)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network: GMGM_TOPK_ORTHO needs a square V (r == d)");
+  if (prec != GMGM_FP32 && r > 64 && !(flags & GMGM_TOPK_ORTHO))
     return fail(h, GMGM_E_ARG, "gmgm_topk_network: tensor-core screen supports r <= 64");
   GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  if (flags & GMGM_TOPK_ORTHO) {
+    int rc = gmgm::ensure_scratch(h, gmgm::topk_ortho_scratch_bytes(d, r, k, prec));
+    if (rc) return rc;
+    return gmgm::topk_run_ortho(h, d, r, V, v_fp64, ldv, psi, k, prec, idx_out, val_out, h->scratch, stats);
+  }
   int rc = gmgm::ensure_scratch(h, gmgm::topk_scratch_bytes(d, r, k, prec));
   if (rc) return rc;
   return gmgm::topk_run(h, d, r, V, v_fp64, ldv, psi, k, prec, idx_out, val_out, h->scratch, stats);

@@ -103,5 +103,11 @@ size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec);
 int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
              const double* psi, int32_t k, gmgm_prec prec, int32_t* idx, float* val,
              void* scratch, gmgm_topk_stats* st);
+// V square (r == d) with orthonormal columns: Psi = c I + V diag(psi - c) V^T
+// with c = min psi; the network is that of the columns with psi > c
+size_t topk_ortho_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec);
+int topk_run_ortho(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
+                   const double* psi, int32_t k, gmgm_prec prec, int32_t* idx, float* val,
+                   void* scratch, gmgm_topk_stats* st);
 
 }  // namespace gmgm

@@ -572,4 +572,110 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   return GMGM_OK;
 }
 
+
+// ---- square orthonormal V: split off c I --------------------------------------
+
+namespace {
+
+// c = min psi; the columns with psi_q > c in order (cols, psi_q - c), their
+// count in *count.  One block.
+__global__ void ortho_compact_kernel(const double* __restrict__ psi, int r, double* __restrict__ psi_free,
+                                     int* __restrict__ cols, int* __restrict__ count) {
+  __shared__ double red[33];
+  __shared__ int base;
+  double m = 1.0e308;
+  for (int q = threadIdx.x; q < r; q += blockDim.x) m = fmin(m, psi[q]);
+  const double c = -block_max(-m, red);
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int q0 = 0; q0 < r; q0 += blockDim.x) {
+    const int q = q0 + threadIdx.x;
+    const bool keep = q < r && psi[q] > c;
+    // order-preserving compaction: warp ballots, then warps in order
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    __shared__ int wcount[32];
+    if (lane == 0) wcount[threadIdx.x >> 5] = __popc(bal);
+    __syncthreads();
+    int before = base;
+    for (int w = 0; w < int(threadIdx.x >> 5); ++w) before += wcount[w];
+    if (keep) {
+      const int pos = before + __popc(bal & ((1u << lane) - 1u));
+      cols[pos] = q;
+      psi_free[pos] = psi[q] - c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) t += wcount[w];
+      base += t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+__global__ void gather_cols_kernel(const void* V, int v64, int64_t ldv, int64_t d, const int* __restrict__ cols,
+                                   int rf, double* __restrict__ Vf) {
+  const int64_t total = d * rf;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / rf;
+    const int q = int(e - i * rf);
+    Vf[e] = vload(V, v64, i * ldv + cols[q]);
+  }
+}
+
+// Every off-diagonal entry is exactly zero: the k lowest columns j != i
+// (the tie rule), value 0.
+__global__ void tie_rows_kernel(int64_t d, int k, int32_t* __restrict__ idx, float* __restrict__ val) {
+  const int64_t total = d * k;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / k;
+    const int c = int(e - i * k);
+    idx[e] = int32_t(c < i ? c : c + 1);
+    val[e] = 0.f;
+  }
+}
+
+}  // namespace
+
+size_t topk_ortho_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec) {
+  return Carve::round(size_t(d) * r * 8) + Carve::round(size_t(r) * 8) + Carve::round(size_t(r) * 4) +
+         Carve::round(64) + topk_scratch_bytes(d, r, k, prec == GMGM_BF16 && r > 64 ? GMGM_FP32 : prec) + 4096;
+}
+
+int topk_run_ortho(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv, const double* psi,
+                   int32_t k, gmgm_prec prec, int32_t* idx, float* val, void* scratch, gmgm_topk_stats* st) {
+  cudaStream_t s = h->stream;
+  Carve c(scratch);
+  double* Vf = c.take<double>(size_t(d) * r);
+  double* psif = c.take<double>(r);
+  int* cols = c.take<int>(r);
+  int* cnt = c.take<int>(16);
+  void* rest = c.take<char>(topk_scratch_bytes(d, r, k, prec == GMGM_BF16 && r > 64 ? GMGM_FP32 : prec));
+  ortho_compact_kernel<<<1, 1024, 0, s>>>(psi, r, psif, cols, cnt);
+  note_launch(1);
+  int rf = 0;
+  GMGM_CUDA_TRY(h, cudaMemcpyAsync(&rf, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (rf == 0) {
+    const unsigned blocks = unsigned(std::min<int64_t>((d * k + 255) / 256, int64_t(h->num_sms) * 8));
+    tie_rows_kernel<<<blocks, 256, 0, s>>>(d, k, idx, val);
+    note_launch(1);
+    GMGM_CUDA_TRY(h, cudaGetLastError());
+    if (st) {
+      GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
+      *st = gmgm_topk_stats{0, 0, 0, 0.0, 0.0, 0.0};
+    }
+    return GMGM_OK;
+  }
+  {
+    const unsigned blocks = unsigned(std::min<int64_t>((d * rf + 255) / 256, int64_t(h->num_sms) * 16));
+    gather_cols_kernel<<<blocks, 256, 0, s>>>(V, v_fp64, ldv, d, cols, rf, Vf);
+    note_launch(1);
+  }
+  const gmgm_prec p2 = prec == GMGM_BF16 && rf > 64 ? GMGM_FP32 : prec;
+  return topk_run(h, d, rf, Vf, 1, rf, psif, k, p2, idx, val, rest, st);
+}
+
 }  // namespace gmgm

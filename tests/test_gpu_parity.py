@@ -309,6 +309,41 @@ def test_topk_bf16_repair_screen_certifies_near_ties(g, cuda_dev):
     assert st["rows_exact"] <= st["rows_uncertified"] // 4, st
 
 
+def _orthonormal(d, seed):
+    q, _ = np.linalg.qr(_rng(seed).standard_normal((d, d)))
+    return q
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_topk_ortho_split_of_clipped_eigenvalues(g, cuda_dev, prec):
+    # full-rank axis with 250 of 300 eigenvalues at the box: the network of
+    # c I + V diag(psi - c) V^T is that of the 50 free columns (the tensor
+    # screen handles them at r = 50 for a BF16 request)
+    d, k = 300, 10
+    V = _orthonormal(d, 71)
+    psi = np.full(d, 1e-3)
+    free = _rng(72).choice(d, 50, replace=False)
+    psi[free] = _rng(73).uniform(0.5, 2.0, 50)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(psi).to(cuda_dev), k,
+                                  g.FP32 if prec == "fp32" else g.BF16, ortho=True)
+    frac = _check_topk(V, psi, k, idx.cpu().numpy(), val.cpu().numpy())
+    assert frac > 0.9
+    assert st["screen_err_ratio"] <= 1.0
+
+
+def test_topk_ortho_all_at_the_minimum_is_all_ties(g, cuda_dev):
+    # psi = c everywhere: Psi = c I, every off-diagonal entry is exactly 0 and
+    # each row takes the k lowest columns j != i with value 0
+    d, k = 257, 20
+    V = _orthonormal(d, 74)
+    psi = np.full(d, 3e-9)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(psi).to(cuda_dev), k,
+                                  ortho=True)
+    want = np.array([[c if c < i else c + 1 for c in range(k)] for i in range(d)])
+    assert np.array_equal(idx.cpu().numpy(), want)
+    assert np.all(val.cpu().numpy() == 0.0)
+
+
 def test_topk_argument_errors(g, cuda_dev):
     V = torch.zeros(10, 3, device=cuda_dev)
     psi = torch.ones(3, dtype=torch.float64, device=cuda_dev)
@@ -318,6 +353,8 @@ def test_topk_argument_errors(g, cuda_dev):
         g.topk_network(V, psi, 33)      # k > 32
     with pytest.raises(g.GmgmError):
         g.topk_network(V, psi, 3, g.BF16X3)  # no split-product screen
+    with pytest.raises(g.GmgmError):
+        g.topk_network(V, psi, 3, ortho=True)  # the orthonormal split needs a square V
     with pytest.raises(g.GmgmError):
         g.topk_network(torch.zeros(100, 65, device=cuda_dev), torch.ones(65, dtype=torch.float64, device=cuda_dev),
                        3, g.BF16)       # tensor-core screen needs r <= 64
