@@ -279,7 +279,7 @@ def main():
         ev[1].record(stream)
         S = g.gram(x, g.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
         ev[2].record(stream)
-        e_all, W = g.spectra(S, a.genes, True, h=h)
+        e_all, W = g.spectra(S, a.genes, rv=a.r_cells, h=h)
         ev[3].record(stream)
         U = g.lift(x, W[:, :a.r_cells].contiguous(), e_all[:a.r_cells].contiguous(), a.r_cells, h=h)
         ev[4].record(stream)
@@ -289,7 +289,7 @@ def main():
         ev[5].record(stream)
         g.topk_network(U, lr, a.k_cells, topk_prec, h=h)
         ev[6].record(stream)
-        g.topk_network(W, lc, a.k_genes, g.FP32, ortho=True, h=h)
+        g.topk_network_gram(S, lc, a.k_genes, g.FP32, h=h)
         ev[7].record(stream)
         torch.cuda.synchronize()
         out = {n: round(ev[i].elapsed_time(ev[i + 1]), 3) for i, n in enumerate(names)}

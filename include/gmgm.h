@@ -166,13 +166,16 @@ int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec,
  * back-transformation.  Theorem 1: the top-r eigenvectors of S_l are those of
  * the MLE Psi_l.
  *   evals  device, r FP64, the r largest eigenvalues, descending.
- *   evecs  device, d x r FP64 row-major (column c is the eigenvector of
- *          evals[c]), leading dimension ldv >= r; may be NULL (values only).
+ *   rv     0 <= rv <= r: eigenvectors are formed for the rv largest
+ *          eigenvalues only (the back-transformation is O(d^2) per vector).
+ *   evecs  device, d x rv FP64 row-major (column c is the eigenvector of
+ *          evals[c]), leading dimension ldv >= rv; NULL iff rv = 0.
  * 1 <= r <= d <= 8192.  Eigenvector signs are arbitrary.  The call uses a
  * cooperative launch.  Errors: GMGM_E_ARG, GMGM_E_CUDA; device TIMEOUT bit
  * if a grid barrier gave up. */
 int gmgm_spectra(gmgm_handle* h, int64_t d, const double* S, int64_t lds,
-                 int32_t r, double* evals, double* evecs, int64_t ldv);
+                 int32_t r, double* evals, int32_t rv, double* evecs,
+                 int64_t ldv);
 
 /* Dual lift (Section "Algorithm": eigenvectors of S_l are singular vectors
  * of mat_l[D]; Algorithm 1 takes the top-r left singular vectors): for the
@@ -386,6 +389,27 @@ int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r,
                       const double* psi, int32_t k, gmgm_prec prec,
                       uint32_t flags, int32_t* idx_out, float* val_out,
                       gmgm_topk_stats* stats);
+
+/* The network of a full-rank axis straight from its Gram: Psi = W diag(psi)
+ * W^T with W the d x d orthonormal eigenvectors of S (psi[j] pairs with the
+ * j-th largest eigenvalue of S; the axis' full spectrum).  As for
+ * GMGM_TOPK_ORTHO, Psi = c I + W diag(psi - c) W^T with c = min psi, and
+ * the off-diagonal entries depend only on the eigenvectors whose psi
+ * exceeds c: only those are formed (tridiagonalisation of S, bisection and
+ * inverse iteration for those eigenvalues, back-transformation), then the
+ * network follows as in gmgm_topk_network; with none, every off-diagonal
+ * entry is 0 and each row takes the k lowest columns j != i (values 0).
+ * Eigenvalues of S closer than 1e-7 ||S|| whose psi fall on both sides of
+ * c are a boundary case: their vectors are orthogonalised within the formed
+ * set only.
+ *   S     device, d x d FP64 (lower triangle read), leading dimension lds.
+ *   psi   device, d FP64.
+ *   k, prec, idx_out, val_out, stats: as gmgm_topk_network.
+ * 2 <= d <= 8192.  Errors: GMGM_E_ARG, GMGM_E_CUDA. */
+int gmgm_topk_network_gram(gmgm_handle* h, int64_t d, const double* S,
+                           int64_t lds, const double* psi, int32_t k,
+                           gmgm_prec prec, int32_t* idx_out, float* val_out,
+                           gmgm_topk_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -81,7 +81,7 @@ SIGNATURES = {
     "gmgm_preprocess": (c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp,
                                 c_i64, c_vp]),
     "gmgm_gram": (c_int, [c_vp, ctypes.POINTER(Matrix), c_int, c_int, c_vp, c_i64, c_int]),
-    "gmgm_spectra": (c_int, [c_vp, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_i64]),
+    "gmgm_spectra": (c_int, [c_vp, c_i64, c_vp, c_i64, c_i32, c_vp, c_i32, c_vp, c_i64]),
     "gmgm_lift": (c_int, [c_vp, ctypes.POINTER(Matrix), c_i32, c_vp, c_i64, c_vp, c_vp, c_i64]),
     "gmgm_eigsolve": (c_int, [c_vp, ctypes.POINTER(Problem), ctypes.POINTER(c_vp),
                               ctypes.POINTER(SolveOpts), ctypes.POINTER(c_vp),
@@ -98,6 +98,8 @@ SIGNATURES = {
     "gmgm_warmstart_infer": (c_int, [c_vp, c_vp, c_vp, c_i32, c_vp, c_i32, c_dbl, c_vp, c_vp]),
     "gmgm_topk_network": (c_int, [c_vp, c_i64, c_i32, c_vp, c_int, c_i64, c_vp, c_i32, c_int,
                                   ctypes.c_uint32, c_vp, c_vp, ctypes.POINTER(TopkStats)]),
+    "gmgm_topk_network_gram": (c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i32, c_int, c_vp, c_vp,
+                                       ctypes.POINTER(TopkStats)]),
 }
 
 _lib = None

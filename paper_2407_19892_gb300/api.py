@@ -151,16 +151,19 @@ def gram(x: torch.Tensor = None, side: int = L.SIDE_COLS, prec: int = L.FP32, xt
 
 # ---- spectra ---------------------------------------------------------------
 
-def spectra(S: torch.Tensor, r: int, vectors: bool = True, h: Handle = None):
-    """Top-r eigenpairs (descending) of a symmetric FP64 matrix on the GPU."""
+def spectra(S: torch.Tensor, r: int, vectors: bool = True, rv: int = None, h: Handle = None):
+    """The r largest eigenvalues (descending) of a symmetric FP64 matrix on
+    the GPU and the eigenvectors of the rv largest (rv = r when vectors,
+    else 0)."""
     h = h or handle(S.device)
     _need_cuda(S, torch.float64, "S")
     if S.stride(1) != 1:
         S = S.contiguous()
     d = S.shape[0]
+    rv = (r if vectors else 0) if rv is None else rv
     ev = torch.empty(r, dtype=torch.float64, device=S.device)
-    W = torch.empty(d, r, dtype=torch.float64, device=S.device) if vectors else None
-    h.check(h.lib.gmgm_spectra(h.h, d, _ptr(S), S.stride(0), r, _ptr(ev), _ptr(W), r))
+    W = torch.empty(d, rv, dtype=torch.float64, device=S.device) if rv > 0 else None
+    h.check(h.lib.gmgm_spectra(h.h, d, _ptr(S), S.stride(0), r, _ptr(ev), rv, _ptr(W), max(rv, 1)))
     return ev, W
 
 
@@ -238,6 +241,24 @@ def topk_network(V: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32,
     return idx, val, st.as_dict()
 
 
+def topk_network_gram(S: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32, h: Handle = None):
+    """Network of a full-rank axis from its Gram S: top-k of |W diag(psi) W^T|
+    with W the eigenvectors of S (psi in descending eigenvalue order); only
+    the eigenvectors whose psi exceeds min psi are formed."""
+    h = h or handle(S.device)
+    _need_cuda(S, torch.float64, "S")
+    if S.stride(1) != 1:
+        S = S.contiguous()
+    _need_cuda(psi, torch.float64, "psi")
+    d = S.shape[0]
+    idx = torch.empty(d, k, dtype=torch.int32, device=S.device)
+    val = torch.empty(d, k, dtype=torch.float32, device=S.device)
+    st = L.TopkStats()
+    h.check(h.lib.gmgm_topk_network_gram(h.h, d, _ptr(S), S.stride(0), _ptr(psi.contiguous()), k, prec, _ptr(idx),
+                                         _ptr(val), ctypes.byref(st)))
+    return idx, val, st.as_dict()
+
+
 # ---- the whole two-axis fit -----------------------------------------------------
 
 @dataclass
@@ -245,7 +266,7 @@ class TwoAxisResult:
     e_rows: torch.Tensor
     v_rows: torch.Tensor
     e_cols: torch.Tensor
-    v_cols: torch.Tensor
+    v_cols: torch.Tensor      # None when the gene axis is at full rank (not formed)
     lam_rows: torch.Tensor
     lam_cols: torch.Tensor
     idx_rows: torch.Tensor
@@ -255,6 +276,7 @@ class TwoAxisResult:
     solve: dict = field(default_factory=dict)
     topk_rows_stats: dict = field(default_factory=dict)
     topk_cols_stats: dict = field(default_factory=dict)
+    s_cols: torch.Tensor = None  # the gene Gram X^T X (FP64)
 
 
 def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols: int,
@@ -268,8 +290,12 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
     h = h or handle(x.device)
     S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, h=h)
     rmax = max(r_rows, r_cols)
-    ev, W = spectra(S, rmax, True, h=h)
-    e_cols, v_cols = ev[:r_cols].contiguous(), W[:, :r_cols].contiguous()
+    full = r_cols == S.shape[0]
+    # eigenvectors: the cell axis' r_rows for the lift; the gene axis' only
+    # when it is truncated (at full rank its network comes from S directly)
+    ev, W = spectra(S, rmax, rv=r_rows if full else rmax, h=h)
+    e_cols = ev[:r_cols].contiguous()
+    v_cols = None if full else W[:, :r_cols].contiguous()
     e_rows = ev[:r_rows].contiguous()
     if init is None and warm_params is not None:
         i0, i1 = torch.empty_like(e_rows), torch.empty_like(e_cols)
@@ -280,9 +306,11 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
     (lam_rows, lam_cols), st = eigsolve([e_rows, e_cols], [(0, 1)], tol=tol, fp32_phase=fp32_phase,
                                         init=init, h=h)
     ir, vr, sr = topk_network(v_rows, lam_rows, k_rows, topk_prec, h=h)
-    # the gene axis at full rank: V = W is square and orthonormal
-    ic, vc, sc = topk_network(v_cols, lam_cols, k_cols, L.FP32, ortho=v_cols.shape[0] == v_cols.shape[1], h=h)
-    return TwoAxisResult(e_rows, v_rows, e_cols, v_cols, lam_rows, lam_cols, ir, vr, ic, vc, st, sr, sc)
+    if full:
+        ic, vc, sc = topk_network_gram(S, lam_cols, k_cols, L.FP32, h=h)
+    else:
+        ic, vc, sc = topk_network(v_cols, lam_cols, k_cols, L.FP32, h=h)
+    return TwoAxisResult(e_rows, v_rows, e_cols, v_cols, lam_rows, lam_cols, ir, vr, ic, vc, st, sr, sc, S)
 
 
 # ---- several modalities sharing the cell axis; one K-axis tensor ---------------
@@ -290,7 +318,10 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
 @dataclass
 class MultiAxisResult:
     E: list        # per axis, FP64 descending
-    V: list        # per axis, eigenvectors as columns (cells: FP32 lift; others FP64)
+    V: list        # per axis, eigenvectors as columns (cells: FP32 lift); None for a full-rank
+                   # axis, whose network comes from its Gram
+    S: list        # per axis, the Gram its spectrum and network come from (cells: the Gram of the
+                   # concatenation; a feature axis: its diagonal block)
     lam: list      # per axis, FP64
     idx: list      # per axis, int32 [d_l, k_l] (None where no network was asked)
     val: list      # per axis, FP32 [d_l, k_l]
@@ -332,25 +363,29 @@ def fit_multimodal(counts, r_cells: int, ks, gram_prec: int = L.BF16X3, topk_pre
         off += p
     S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
     e_c, W_c = spectra(S, r_cells, True, h=h)
-    E, V = [e_c], [lift(x, W_c, e_c, r_cells, h=h)]
+    E, V, Ss = [e_c], [lift(x, W_c, e_c, r_cells, h=h)], [S]
     off = 0
     for p in ps:
-        e, W = spectra(S[off:off + p, off:off + p], p, True, h=h)
+        Sb = S[off:off + p, off:off + p]
+        e, _ = spectra(Sb, p, vectors=False, h=h)
         E.append(e)
-        V.append(W)
+        V.append(None)
+        Ss.append(Sb)
         off += p
     lams, st = eigsolve(E, [(0, m + 1) for m in range(len(ps))], tol=tol, h=h)
     idx, val, sts = [], [], []
     for a in range(len(E)):
         if ks[a]:
-            # feature axes at full rank: square orthonormal W
-            i, v, t = topk_network(V[a], lams[a], ks[a], topk_prec if a == 0 else L.FP32, ortho=a > 0, h=h)
+            if a == 0:
+                i, v, t = topk_network(V[0], lams[0], ks[0], topk_prec, h=h)
+            else:  # a feature axis at full rank
+                i, v, t = topk_network_gram(Ss[a], lams[a], ks[a], L.FP32, h=h)
         else:
             i = v = t = None
         idx.append(i)
         val.append(v)
         sts.append(t)
-    return MultiAxisResult(E, V, lams, idx, val, st, sts)
+    return MultiAxisResult(E, V, Ss, lams, idx, val, st, sts)
 
 
 def fit_tensor(t: torch.Tensor, ks, tol: float = 1e-9, h: Handle = None) -> MultiAxisResult:
@@ -367,19 +402,15 @@ def fit_tensor(t: torch.Tensor, ks, tol: float = 1e-9, h: Handle = None) -> Mult
     Ss = [gram(t.reshape(d0, d1 * d2), L.SIDE_ROWS, L.FP32, h=h),
           gram(t, L.SIDE_ROWS, L.FP32, h=h),
           gram(t.reshape(d0 * d1, d2), L.SIDE_COLS, L.FP32, h=h)]
-    E, V = [], []
-    for S in Ss:
-        e, W = spectra(S, S.shape[0], True, h=h)
-        E.append(e)
-        V.append(W)
+    E = [spectra(S, S.shape[0], vectors=False, h=h)[0] for S in Ss]
     lams, st = eigsolve(E, [(0, 1, 2)], tol=tol, h=h)
     idx, val, sts = [], [], []
     for a in range(3):
         if ks[a]:
-            i, v, s_ = topk_network(V[a], lams[a], ks[a], L.FP32, ortho=True, h=h)
+            i, v, s_ = topk_network_gram(Ss[a], lams[a], ks[a], L.FP32, h=h)
         else:
             i = v = s_ = None
         idx.append(i)
         val.append(v)
         sts.append(s_)
-    return MultiAxisResult(E, V, lams, idx, val, st, sts)
+    return MultiAxisResult(E, [None] * 3, Ss, lams, idx, val, st, sts)

@@ -169,14 +169,16 @@ int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec, do
 }
 
 int gmgm_spectra(gmgm_handle* h, int64_t d, const double* S, int64_t lds, int32_t r,
-                 double* evals, double* evecs, int64_t ldv) {
+                 double* evals, int32_t rv, double* evecs, int64_t ldv) {
   if (!h) return GMGM_E_ARG;
-  if (d < 1 || d > 8192 || r < 1 || r > d || !S || !evals || lds < d || (evecs && ldv < r))
-    return fail(h, GMGM_E_ARG, "gmgm_spectra: need 1 <= r <= d <= 8192, lds >= d, ldv >= r");
+  if (d < 1 || d > 8192 || r < 1 || r > d || !S || !evals || lds < d)
+    return fail(h, GMGM_E_ARG, "gmgm_spectra: need 1 <= r <= d <= 8192, lds >= d");
+  if (rv < 0 || rv > r || (rv > 0) != (evecs != nullptr) || (rv > 0 && ldv < rv))
+    return fail(h, GMGM_E_ARG, "gmgm_spectra: need 0 <= rv <= r, evecs non-null iff rv > 0, ldv >= rv");
   GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
-  int rc = gmgm::ensure_scratch(h, gmgm::eig_scratch_bytes(d, r));
+  int rc = gmgm::ensure_scratch(h, gmgm::eig_scratch_bytes(d, r, rv));
   if (rc) return rc;
-  GMGM_CUDA_TRY(h, gmgm::launch_eig(h, d, S, lds, r, evals, evecs, ldv, h->scratch));
+  GMGM_CUDA_TRY(h, gmgm::launch_eig(h, d, S, lds, r, evals, nullptr, rv, evecs, ldv, h->scratch));
   return GMGM_OK;
 }
 
@@ -369,6 +371,20 @@ int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v
   int rc = gmgm::ensure_scratch(h, gmgm::topk_scratch_bytes(d, r, k, prec));
   if (rc) return rc;
   return gmgm::topk_run(h, d, r, V, v_fp64, ldv, psi, k, prec, idx_out, val_out, h->scratch, stats);
+}
+
+int gmgm_topk_network_gram(gmgm_handle* h, int64_t d, const double* S, int64_t lds, const double* psi,
+                           int32_t k, gmgm_prec prec, int32_t* idx_out, float* val_out, gmgm_topk_stats* stats) {
+  if (!h) return GMGM_E_ARG;
+  if (d < 2 || d > 8192 || !S || !psi || !idx_out || !val_out || lds < d)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network_gram: need 2 <= d <= 8192, lds >= d, non-null buffers");
+  if (k < 1 || k > 32 || k >= d) return fail(h, GMGM_E_ARG, "gmgm_topk_network_gram: need 1 <= k <= 32, k < d");
+  if (prec != GMGM_FP32 && prec != GMGM_BF16)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network_gram: prec must be FP32 or BF16");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, gmgm::topk_gram_scratch_bytes(d, k, prec));
+  if (rc) return rc;
+  return gmgm::topk_run_gram(h, d, S, lds, psi, k, prec, idx_out, val_out, h->scratch, stats);
 }
 
 }  // extern "C"

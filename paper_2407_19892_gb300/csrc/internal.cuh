@@ -74,9 +74,12 @@ cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec,
 int gram_tc_splits(gmgm_handle* h, const gmgm_matrix* m);
 size_t gram_tc_scratch_bytes(gmgm_handle* h, const gmgm_matrix* m);
 
-size_t eig_scratch_bytes(int64_t d, int32_t r);
-cudaError_t launch_eig(gmgm_handle* h, int64_t d, const double* S, int64_t lds, int32_t r,
-                       double* evals, double* evecs, int64_t ldv, void* scratch);
+// FP64 eigendecomposition of S: the nval largest eigenvalues (descending)
+// and eigenvectors for the nvec largest, or for the ascending eigenvalue
+// indices vlist[0..nvec) (device) when vlist is given
+size_t eig_scratch_bytes(int64_t d, int32_t nval, int32_t nvec);
+cudaError_t launch_eig(gmgm_handle* h, int64_t d, const double* S, int64_t lds, int32_t nval, double* evals,
+                       const int* vlist, int32_t nvec, double* evecs, int64_t ldv, void* scratch);
 
 cudaError_t launch_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const double* W,
                         int64_t ldw, const double* E, float* U, int64_t ldu, float* wscr);
@@ -106,6 +109,11 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
 // V square (r == d) with orthonormal columns: Psi = c I + V diag(psi - c) V^T
 // with c = min psi; the network is that of the columns with psi > c
 size_t topk_ortho_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec);
+// the network of W diag(psi) W^T for W the eigenvectors of S (full rank),
+// eigenvectors formed only for the eigenvalues whose psi exceeds min psi
+size_t topk_gram_scratch_bytes(int64_t d, int32_t k, gmgm_prec prec);
+int topk_run_gram(gmgm_handle* h, int64_t d, const double* S, int64_t lds, const double* psi, int32_t k,
+                  gmgm_prec prec, int32_t* idx, float* val, void* scratch, gmgm_topk_stats* st);
 int topk_run_ortho(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
                    const double* psi, int32_t k, gmgm_prec prec, int32_t* idx, float* val,
                    void* scratch, gmgm_topk_stats* st);

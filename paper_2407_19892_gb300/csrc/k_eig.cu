@@ -239,11 +239,13 @@ __device__ __forceinline__ int sturm_count(const double* dv, const double* e2, i
 
 constexpr int kMS = 8;  // lanes per eigenvalue (9-way multisection)
 
-// Lanes in groups of kMS find the ascending eigenvalues j0 + group: each
-// round evaluates kMS interior points of the current interval and keeps the
-// sub-interval holding eigenvalue j (counts are monotone in x).
+// Lanes in groups of kMS find the ascending eigenvalues j0 + group (or
+// jlist[group]): each round evaluates kMS interior points of the current
+// interval and keeps the sub-interval holding eigenvalue j (counts are
+// monotone in x).
 __global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __restrict__ e2_g, int n, int j0,
-                              int cnt, const double* __restrict__ info, double* __restrict__ lam) {
+                              const int* __restrict__ jlist, int cnt, const double* __restrict__ info,
+                              double* __restrict__ lam) {
   extern __shared__ double sm[];
   double* dv = sm;
   double* e2 = sm + n;
@@ -256,7 +258,8 @@ __global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __r
   const int sub = lane % kMS, gbase = lane - sub;
   const int group = (blockIdx.x * blockDim.x + threadIdx.x) / kMS;
   const bool active = group < cnt;
-  const int j = j0 + (active ? group : cnt - 1);
+  const int gi = active ? group : cnt - 1;
+  const int j = jlist ? jlist[gi] : j0 + gi;
   const double floor_abs = 4.0 * info[2];
   double lo = info[0], hi = info[1];
   for (int round = 0; round < 64; ++round) {
@@ -457,14 +460,17 @@ __global__ void back_transform_kernel(const double* __restrict__ Vh, const doubl
   }
 }
 
-// evals[c] = lam[cnt-1-c]; evecs[i*ldv + c] = Zc[(cnt-1-c)*n + i]
-__global__ void output_kernel(const double* __restrict__ lam, const double* __restrict__ Zc, int n, int cnt,
-                              double* __restrict__ evals, double* __restrict__ evecs, int64_t ldv) {
+// evals[c] = lam[cnt-1-c] (descending)
+__global__ void values_kernel(const double* __restrict__ lam, int cnt, double* __restrict__ evals) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cnt) evals[c] = lam[cnt - 1 - c];
+}
+
+// evecs[i*ldv + c] = Zc[(cnt-1-c)*n + i]
+__global__ void output_kernel(const double* __restrict__ Zc, int n, int cnt, double* __restrict__ evecs,
+                              int64_t ldv) {
   __shared__ double tile[32][33];
   const int c0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
-  if (blockIdx.y == 0 && threadIdx.y == 0 && c0 + int(threadIdx.x) < cnt)
-    evals[c0 + threadIdx.x] = lam[cnt - 1 - (c0 + threadIdx.x)];
-  if (!evecs) return;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int c = c0 + r, i = i0 + threadIdx.x;
     tile[r][threadIdx.x] = (c < cnt && i < n) ? Zc[int64_t(cnt - 1 - c) * n + i] : 0.0;
@@ -479,14 +485,14 @@ __global__ void output_kernel(const double* __restrict__ lam, const double* __re
 constexpr int kInvBatch = 4096;
 
 struct EigScratch {
-  double *A, *Vh, *tau, *dv, *ev, *e2, *P, *info, *lam, *u0, *u1, *u2, *Z, *Zc;
+  double *A, *Vh, *tau, *dv, *ev, *e2, *P, *info, *lam, *lamv, *u0, *u1, *u2, *Z, *Zc;
   size_t bytes;
 };
 
-EigScratch carve_eig(void* base, int64_t d, int32_t r) {
+EigScratch carve_eig(void* base, int64_t d, int32_t nval, int32_t nvec) {
   Carve c(base);
   EigScratch s;
-  const int64_t B = std::min<int64_t>(r, kInvBatch);
+  const int64_t B = std::max<int64_t>(1, std::min<int64_t>(nvec, kInvBatch));
   s.A = c.take<double>(d * d);
   s.Vh = c.take<double>(d * d);
   s.tau = c.take<double>(d);
@@ -495,29 +501,32 @@ EigScratch carve_eig(void* base, int64_t d, int32_t r) {
   s.e2 = c.take<double>(d);
   s.P = c.take<double>(2 * d);
   s.info = c.take<double>(8);
-  s.lam = c.take<double>(r);
+  s.lam = c.take<double>(std::max(nval, 1));
+  s.lamv = c.take<double>(std::max(nvec, 1));
   s.u0 = c.take<double>(d * B);
   s.u1 = c.take<double>(d * B);
   s.u2 = c.take<double>(d * B);
   s.Z = c.take<double>(d * B);
-  s.Zc = c.take<double>(d * r);
+  s.Zc = c.take<double>(d * std::max(nvec, 1));
   s.bytes = c.off + 256;
   return s;
 }
 
 }  // namespace
 
-size_t eig_scratch_bytes(int64_t d, int32_t r) { return carve_eig(nullptr, d, r).bytes; }
+size_t eig_scratch_bytes(int64_t d, int32_t nval, int32_t nvec) { return carve_eig(nullptr, d, nval, nvec).bytes; }
 
-cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds, int32_t r, double* evals,
-                       double* evecs, int64_t ldv, void* scratch) {
+cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds, int32_t nval, double* evals,
+                       const int* vlist, int32_t nvec, double* evecs, int64_t ldv, void* scratch) {
   const int n = int(d64);
   cudaStream_t st = h->stream;
-  EigScratch s = carve_eig(scratch, d64, r);
+  EigScratch s = carve_eig(scratch, d64, nval, nvec);
   cudaError_t e;
+  int launches = 0;
   {
     dim3 b(32, 8), g(unsigned((n + 31) / 32), unsigned((n + 7) / 8));
     copy_sym_kernel<<<g, b, 0, st>>>(S, lds, n, s.A);
+    ++launches;
   }
   if ((e = cudaMemsetAsync(s.Vh, 0, size_t(n) * n * sizeof(double), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(s.tau, 0, size_t(n) * sizeof(double), st)) != cudaSuccess) return e;
@@ -551,38 +560,53 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
     tiny_tridiag_kernel<<<1, 1, 0, st>>>(s.A, n, s.dv, s.ev);
   }
   tri_info_kernel<<<1, 256, 0, st>>>(s.dv, s.ev, n, s.e2, s.info);
-  const int j0 = n - r;
-  {
-    const size_t smem = size_t(2) * n * sizeof(double);
-    if ((e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) !=
-        cudaSuccess)
-      return e;
-    const int tpb = 64;  // small blocks: the groups spread over every SM
-    const int64_t threads = int64_t(r) * kMS;
-    bisect_kernel<<<unsigned((threads + tpb - 1) / tpb), tpb, smem, st>>>(s.dv, s.e2, n, j0, r, s.info, s.lam);
+  launches += 2;
+  const size_t bsmem = size_t(2) * n * sizeof(double);
+  if ((e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsmem))) !=
+      cudaSuccess)
+    return e;
+  const int tpb = 64;  // small blocks: the groups spread over every SM
+  if (nval > 0) {
+    // the nval largest eigenvalues, ascending in lam
+    const int64_t threads = int64_t(nval) * kMS;
+    bisect_kernel<<<unsigned((threads + tpb - 1) / tpb), tpb, bsmem, st>>>(s.dv, s.e2, n, n - nval, nullptr, nval,
+                                                                          s.info, s.lam);
+    values_kernel<<<unsigned((nval + 255) / 256), 256, 0, st>>>(s.lam, nval, evals);
+    launches += 2;
   }
-  const int B = std::min(r, kInvBatch);
-  for (int t0 = 0; t0 < r; t0 += B) {
-    const int cnt = std::min(B, r - t0);
-    inverse_iter_kernel<<<unsigned((cnt + 31) / 32), 32, 0, st>>>(s.dv, s.ev, n, s.lam + t0, cnt, B, s.info,
-                                                                   s.u0, s.u1, s.u2, s.Z, t0);
-    dim3 tb(32, 8), tg(unsigned((cnt + 31) / 32), unsigned((n + 31) / 32));
-    transpose_kernel<<<tg, tb, 0, st>>>(s.Z, n, cnt, B, s.Zc, t0);
-  }
-  cluster_mgs_kernel<<<unsigned(r), 256, 0, st>>>(s.lam, r, s.info, 1e-7, n, s.Zc);
-  if (evecs) {
+  if (nvec > 0) {
+    // targets of the vectors: the nvec largest (reusing lam), or the listed
+    // ascending indices
+    const double* lamv = s.lam + (nval - nvec);
+    if (vlist || nvec > nval) {
+      const int64_t threads = int64_t(nvec) * kMS;
+      bisect_kernel<<<unsigned((threads + tpb - 1) / tpb), tpb, bsmem, st>>>(s.dv, s.e2, n, n - nvec, vlist, nvec,
+                                                                            s.info, s.lamv);
+      lamv = s.lamv;
+      ++launches;
+    }
+    const int B = std::min(nvec, kInvBatch);
+    for (int t0 = 0; t0 < nvec; t0 += B) {
+      const int cnt = std::min(B, nvec - t0);
+      inverse_iter_kernel<<<unsigned((cnt + 31) / 32), 32, 0, st>>>(s.dv, s.ev, n, lamv + t0, cnt, B, s.info,
+                                                                     s.u0, s.u1, s.u2, s.Z, t0);
+      dim3 tb(32, 8), tg(unsigned((cnt + 31) / 32), unsigned((n + 31) / 32));
+      transpose_kernel<<<tg, tb, 0, st>>>(s.Z, n, cnt, B, s.Zc, t0);
+      launches += 2;
+    }
+    cluster_mgs_kernel<<<unsigned(nvec), 256, 0, st>>>(lamv, nvec, s.info, 1e-7, n, s.Zc);
     int wpb = int(std::min<int64_t>(4, std::max<int64_t>(1, (200 * 1024) / (int64_t(n) * 16))));
     const size_t smem = size_t(wpb) * 2 * n * sizeof(double);
     if ((e = cudaFuncSetAttribute(back_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(smem))) != cudaSuccess)
       return e;
-    back_transform_kernel<<<unsigned((r + 2 * wpb - 1) / (2 * wpb)), wpb * 32, smem, st>>>(s.Vh, s.tau, n, r, s.Zc);
+    back_transform_kernel<<<unsigned((nvec + 2 * wpb - 1) / (2 * wpb)), wpb * 32, smem, st>>>(s.Vh, s.tau, n, nvec,
+                                                                                             s.Zc);
+    dim3 b(32, 8), g(unsigned((nvec + 31) / 32), unsigned((n + 31) / 32));
+    output_kernel<<<g, b, 0, st>>>(s.Zc, n, nvec, evecs, ldv);
+    launches += 3;
   }
-  {
-    dim3 b(32, 8), g(unsigned((r + 31) / 32), unsigned((n + 31) / 32));
-    output_kernel<<<g, b, 0, st>>>(s.lam, s.Zc, n, r, evals, evecs, ldv);
-  }
-  note_launch(6 + 2 * ((r + B - 1) / B) + (evecs ? 1 : 0));
+  note_launch(launches);
   return cudaGetLastError();
 }
 

@@ -639,9 +639,66 @@ __global__ void tie_rows_kernel(int64_t d, int k, int32_t* __restrict__ idx, flo
 
 }  // namespace
 
+namespace {
+
+// ascending eigenvalue indices of the kept columns: cols[] holds descending-
+// order indices q (ascending q); j = d - 1 - q, listed in ascending j
+__global__ void gram_vlist_kernel(const int* __restrict__ cols, const int* __restrict__ count, int d,
+                                  int* __restrict__ vlist) {
+  const int n = *count;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    vlist[t] = d - 1 - cols[n - 1 - t];
+}
+
+}  // namespace
+
+size_t topk_gram_scratch_bytes(int64_t d, int32_t k, gmgm_prec prec) {
+  // compaction buffers, the formed vectors (at most d), the eigensolver and
+  // the network on the formed columns
+  return Carve::round(size_t(d) * 8) + Carve::round(size_t(d) * 4) * 2 + Carve::round(64) +
+         Carve::round(size_t(d) * d * 8) + eig_scratch_bytes(d, 0, int32_t(d)) +
+         topk_scratch_bytes(d, int32_t(d), k, prec) + 4096;
+}
+
+int topk_run_gram(gmgm_handle* h, int64_t d, const double* S, int64_t lds, const double* psi, int32_t k,
+                  gmgm_prec prec, int32_t* idx, float* val, void* scratch, gmgm_topk_stats* st) {
+  cudaStream_t s = h->stream;
+  const int n = int(d);
+  Carve c(scratch);
+  double* psif = c.take<double>(d);
+  int* cols = c.take<int>(d);
+  int* vlist = c.take<int>(d);
+  int* cnt = c.take<int>(16);
+  double* Vf = c.take<double>(size_t(d) * d);
+  void* eig = c.take<char>(eig_scratch_bytes(d, 0, n));
+  void* rest = c.take<char>(topk_scratch_bytes(d, n, k, prec));  // BF16 includes the tensor planes
+  ortho_compact_kernel<<<1, 1024, 0, s>>>(psi, n, psif, cols, cnt);
+  note_launch(1);
+  int rf = 0;
+  GMGM_CUDA_TRY(h, cudaMemcpyAsync(&rf, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
+  if (rf == 0) {
+    const unsigned blocks = unsigned(std::min<int64_t>((d * k + 255) / 256, int64_t(h->num_sms) * 8));
+    tie_rows_kernel<<<blocks, 256, 0, s>>>(d, k, idx, val);
+    note_launch(1);
+    GMGM_CUDA_TRY(h, cudaGetLastError());
+    if (st) {
+      GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
+      *st = gmgm_topk_stats{0, 0, 0, 0.0, 0.0, 0.0};
+    }
+    return GMGM_OK;
+  }
+  gram_vlist_kernel<<<unsigned((rf + 255) / 256), 256, 0, s>>>(cols, cnt, n, vlist);
+  note_launch(1);
+  // vectors for the kept eigenvalues, column t <-> cols[t] (descending order)
+  GMGM_CUDA_TRY(h, launch_eig(h, d, S, lds, 0, nullptr, vlist, rf, Vf, rf, eig));
+  const gmgm_prec p2 = prec == GMGM_BF16 && rf > 64 ? GMGM_FP32 : prec;
+  return topk_run(h, d, rf, Vf, 1, rf, psif, k, p2, idx, val, rest, st);
+}
+
 size_t topk_ortho_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec) {
   return Carve::round(size_t(d) * r * 8) + Carve::round(size_t(r) * 8) + Carve::round(size_t(r) * 4) +
-         Carve::round(64) + topk_scratch_bytes(d, r, k, prec == GMGM_BF16 && r > 64 ? GMGM_FP32 : prec) + 4096;
+         Carve::round(64) + topk_scratch_bytes(d, r, k, prec) + 4096;
 }
 
 int topk_run_ortho(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv, const double* psi,
@@ -652,7 +709,7 @@ int topk_run_ortho(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp
   double* psif = c.take<double>(r);
   int* cols = c.take<int>(r);
   int* cnt = c.take<int>(16);
-  void* rest = c.take<char>(topk_scratch_bytes(d, r, k, prec == GMGM_BF16 && r > 64 ? GMGM_FP32 : prec));
+  void* rest = c.take<char>(topk_scratch_bytes(d, r, k, prec));  // BF16 includes the tensor planes
   ortho_compact_kernel<<<1, 1024, 0, s>>>(psi, r, psif, cols, cnt);
   note_launch(1);
   int rf = 0;

@@ -28,7 +28,9 @@ def run(cuda_dev):
     x, hi, lo, ld_t = g.preprocess(counts, split=True, h=h)
     res = g.fit_two_axis(x, R, GENES, KC, KG, gram_prec=g.BF16X3, topk_prec=g.BF16, xt_hi=hi, xt_lo=lo,
                          ld_t=ld_t, tol=1e-9, warm_params=warmstart.load(cuda_dev), h=h)
-    S = g.gram(x, g.SIDE_COLS, g.BF16X3, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h).cpu().numpy()
+    St = g.gram(x, g.SIDE_COLS, g.BF16X3, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
+    _, Wt = g.spectra(St, GENES, h=h)  # every gene eigenvector, for the stage-wise checks
+    S = St.cpu().numpy()
     rng = np.random.default_rng(5)
     rows = np.sort(rng.choice(CELLS, 64, replace=False))
     cols = np.sort(rng.choice(GENES, 32, replace=False))
@@ -38,14 +40,15 @@ def run(cuda_dev):
         "x_rows": x[torch.from_numpy(rows).to(cuda_dev)].cpu().numpy(),
         "c_rows": counts[torch.from_numpy(rows).to(cuda_dev)].cpu().numpy(),
         "c_cols": counts[:, torch.from_numpy(cols).to(cuda_dev)].cpu().numpy(),
-        "e": res.e_cols.cpu().numpy(), "W": res.v_cols.cpu().numpy(),
+        "e": res.e_cols.cpu().numpy(), "W": Wt.cpu().numpy(),
         "e_rows": res.e_rows.cpu().numpy(), "U": res.v_rows.cpu().numpy(),
         "lr": res.lam_rows.cpu().numpy(), "lc": res.lam_cols.cpu().numpy(),
         "idx_rows": res.idx_rows.cpu().numpy(), "val_rows": res.val_rows.cpu().numpy(),
         "idx_cols": res.idx_cols.cpu().numpy(), "val_cols": res.val_cols.cpu().numpy(),
         "stats_rows": res.topk_rows_stats, "solve": res.solve,
     }
-    del counts, x, hi, lo, res
+    assert res.v_cols is None and torch.equal(res.s_cols, St)
+    del counts, x, hi, lo, res, St, Wt
     torch.cuda.empty_cache()
     return out
 
@@ -72,11 +75,14 @@ def test_spectrum_is_an_eigendecomposition_of_the_gram(run):
 
 
 def test_lift_on_sampled_rows(run):
-    # U_i = x_i W_r diag(e_r)^-1/2 for the cells of the sample
+    # U_i = x_i W_r diag(e_r)^-1/2 for the cells of the sample (eigenvector
+    # signs are arbitrary: the fit's W and this W come from two calls)
     x = np.log1p(run["c_rows"].astype(np.float64)) - run["means"][None, :]
     ref = x @ run["W"][:, :R] / np.sqrt(run["e_rows"])[None, :]
     got = run["U"][run["rows"]]
-    assert np.max(np.abs(got - ref)) <= 1e-5 * np.abs(ref).max()
+    sign = np.sign(np.sum(got * ref, axis=0))
+    assert np.all(sign != 0)
+    assert np.max(np.abs(got - ref * sign[None, :])) <= 1e-5 * np.abs(ref).max()
 
 
 def test_solve_satisfies_kkt(run):

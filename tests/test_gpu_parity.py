@@ -371,6 +371,61 @@ def test_fit_two_axis_c1(g, cuda_dev):
     sg = res.lam_rows.cpu().numpy()[:, None] + res.lam_cols.cpu().numpy()[None, :]
     sr = ref.lam_rows[:, None] + ref.lam_cols[None, :]
     assert np.max(np.abs(sg - sr) / sr) <= 1e-4
-    for V, lam, k, idx, val in ((res.v_rows, res.lam_rows, 10, res.idx_rows, res.val_rows),
-                                (res.v_cols, res.lam_cols, 10, res.idx_cols, res.val_cols)):
-        _check_topk(V.double().cpu().numpy(), lam.cpu().numpy(), k, idx.cpu().numpy(), val.cpu().numpy())
+    # the gene axis is at full rank: its network comes from the Gram (no
+    # vectors returned); the stage-wise check uses FP64 eigenvectors of the
+    # GPU's own Gram
+    assert res.v_cols is None
+    W = np.linalg.eigh(res.s_cols.cpu().numpy())[1][:, ::-1]
+    for V, lam, k, idx, val in ((res.v_rows.double().cpu().numpy(), res.lam_rows, 10, res.idx_rows, res.val_rows),
+                                (W, res.lam_cols, 10, res.idx_cols, res.val_cols)):
+        _check_topk(V, lam.cpu().numpy(), k, idx.cpu().numpy(), val.cpu().numpy())
+
+
+def test_fit_two_axis_truncated_gene_axis(g, cuda_dev):
+    # both axes truncated: the gene vectors come from the spectra call
+    from oracle.fit import fit_two_axis as ofit
+    x, _, _ = planted_c1()
+    x = (x - x.mean(0)).astype(np.float32)
+    res = g.fit_two_axis(torch.from_numpy(x).to(cuda_dev), 30, 60, 10, 10)
+    ref = ofit(x.astype(np.float64), 30, 60, 10, 10)
+    sg = res.lam_rows.cpu().numpy()[:, None] + res.lam_cols.cpu().numpy()[None, :]
+    sr = ref.lam_rows[:, None] + ref.lam_cols[None, :]
+    assert np.max(np.abs(sg - sr) / sr) <= 1e-4
+    assert res.v_cols.shape == (100, 60)
+    _check_topk(res.v_cols.cpu().numpy(), res.lam_cols.cpu().numpy(), 10, res.idx_cols.cpu().numpy(),
+                res.val_cols.cpu().numpy())
+
+
+def test_topk_network_gram_matches_the_square_vectors(g, cuda_dev):
+    # the network from the Gram equals the network of its full eigenvector
+    # matrix (stage-wise, FP64 eigenvectors of the same S), with free
+    # eigenvalues scattered over the spectrum and the rest at the minimum
+    d, k = 220, 12
+    A = _rng(81).standard_normal((400, d))
+    S = A.T @ A
+    psi = np.full(d, 2e-6)
+    free = _rng(82).choice(d, 40, replace=False)
+    psi[free] = _rng(83).uniform(1e-3, 1e-2, 40)
+    idx, val, st = g.topk_network_gram(torch.from_numpy(S).to(cuda_dev), torch.from_numpy(psi).to(cuda_dev), k)
+    W = np.linalg.eigh(S)[1][:, ::-1]
+    frac = _check_topk(W, psi, k, idx.cpu().numpy(), val.cpu().numpy())
+    assert frac > 0.9
+    assert st["screen_err_ratio"] <= 1.0
+    # every psi at the minimum: all ties
+    idx, val, _ = g.topk_network_gram(torch.from_numpy(S).to(cuda_dev), torch.full((d,), 3.0, dtype=torch.float64,
+                                                                                    device=cuda_dev), k)
+    assert np.array_equal(idx.cpu().numpy()[:, 0], np.array([1] + [0] * (d - 1)))
+    assert np.all(val.cpu().numpy() == 0.0)
+
+
+def test_spectra_vectors_for_the_top_rv_only(g, cuda_dev):
+    S = _rng(84).standard_normal((300, 300))
+    S = S @ S.T
+    ev_all, W_all = g.spectra(torch.from_numpy(S).to(cuda_dev), 300, rv=300)
+    ev, W = g.spectra(torch.from_numpy(S).to(cuda_dev), 300, rv=25)
+    assert W.shape == (300, 25)
+    np.testing.assert_array_equal(ev.cpu().numpy(), ev_all.cpu().numpy())
+    _check_eig(S, ev.cpu().numpy()[:25], W.cpu().numpy(), 25)
+    ev0, W0 = g.spectra(torch.from_numpy(S).to(cuda_dev), 300, vectors=False)
+    assert W0 is None
+    np.testing.assert_array_equal(ev0.cpu().numpy(), ev_all.cpu().numpy())
