@@ -7,8 +7,8 @@
 //   3. inverse iteration on T - lambda I (tridiagonal LU with partial
 //      pivoting, one thread per eigenvalue), then modified Gram-Schmidt inside
 //      clusters of nearly equal eigenvalues;
-//   4. back-transformation Z <- Q Z (one warp per two eigenvectors,
-//      reflectors streamed from L2);
+//   4. back-transformation Z <- Q Z in compact WY blocks of 32 reflectors
+//      (one cooperative kernel over every SM, one grid barrier per block);
 //   5. output: the r largest eigenvalues descending, vectors row-major d x r.
 #include <cuda_runtime.h>
 
@@ -411,52 +411,147 @@ __global__ void cluster_mgs_kernel(const double* __restrict__ lam, int cnt, cons
   }
 }
 
-// Z <- H_0 H_1 ... H_{n-3} Z, H_k = I - tau_k v_k v_k^T.  One warp holds two
-// eigenvectors in shared memory, so each reflector read from L2 serves both
-// and the two dot products overlap.
-__global__ void back_transform_kernel(const double* __restrict__ Vh, const double* __restrict__ tau, int n,
-                                      int cnt, double* __restrict__ Zc) {
-  extern __shared__ double sm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int t0 = (blockIdx.x * nwarps + warp) * 2;
-  if (t0 >= cnt) return;
-  const bool two = t0 + 1 < cnt;
-  double* z0 = sm + int64_t(warp) * 2 * n;
-  double* z1 = z0 + n;
-  double* g0 = Zc + int64_t(t0) * n;
-  double* g1 = g0 + n;
-  for (int i = lane; i < n; i += 32) {
-    z0[i] = g0[i];
-    z1[i] = two ? g1[i] : 0.0;
+// ---- blocked back-transformation (compact WY) ------------------------------
+// Q = H_0 H_1 ... H_{n-3} = Q_0 Q_1 ... Q_{B-1}, Q_b = H_{32b} ... H_{32b+31}
+// = I - V_b T_b V_b^T (T_b upper triangular, the forward recurrence
+// T_jj = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j) V_b(:, 0:j)^T v_j).  With
+// U_b = V_b T_b, Z <- Q Z is Z <- Z - U_b (V_b^T Z) for b = B-1 down to 0.
+
+constexpr int kWY = 32;    // reflectors per block
+constexpr int kWYV = 64;   // eigenvectors per pass of the apply kernel
+
+// One CTA per block: G = V_b^T V_b (rows in chunks of 64 through shared
+// memory), T_b, then U_b (stored [b][j][i], rows contiguous).
+__global__ void __launch_bounds__(256) wy_prep_kernel(const double* __restrict__ Vh, const double* __restrict__ tau,
+                                                      int n, double* __restrict__ U) {
+  __shared__ double Vs[kWY][65];
+  __shared__ double G[kWY][kWY + 1];
+  __shared__ double T[kWY][kWY + 1];
+  const int b = blockIdx.x, k0 = b * kWY;
+  const int nb = min(kWY, (n - 2) - k0);
+  // the 528 pairs j <= j2, up to 3 per thread
+  double acc[3] = {0.0, 0.0, 0.0};
+  int pj[3], pk[3];
+  for (int q = 0; q < 3; ++q) {
+    int p = threadIdx.x + q * 256, j = 0;
+    while (p >= kWY - j && j < kWY) p -= kWY - j, ++j;  // p-th pair of row j: (j, j + p)
+    pj[q] = j < kWY ? j : -1;
+    pk[q] = j < kWY ? j + p : -1;
   }
-  __syncwarp();
-  for (int k = n - 3; k >= 0; --k) {
-    const double tk = tau[k];
-    if (tk == 0.0) continue;
-    const double* vk = Vh + int64_t(k) * n;
-    double y0 = 0.0, y1 = 0.0;
-    for (int i = k + 1 + lane; i < n; i += 32) {
-      const double vv = __ldg(vk + i);
-      y0 += vv * z0[i];
-      y1 += vv * z1[i];
+  for (int i0 = k0 + 1; i0 < n; i0 += 64) {
+    for (int e = threadIdx.x; e < kWY * 64; e += blockDim.x) {
+      const int j = e >> 6, r = e & 63;
+      Vs[j][r] = (j < nb && i0 + r < n) ? Vh[int64_t(k0 + j) * n + i0 + r] : 0.0;
     }
+    __syncthreads();
+    for (int q = 0; q < 3; ++q) {
+      if (pj[q] < 0) continue;
+      double sacc = 0.0;
+      for (int r = 0; r < 64; ++r) sacc += Vs[pj[q]][r] * Vs[pk[q]][r];
+      acc[q] += sacc;
+    }
+    __syncthreads();
+  }
+  for (int q = 0; q < 3; ++q)
+    if (pj[q] >= 0) G[pj[q]][pk[q]] = acc[q];
+  for (int e = threadIdx.x; e < kWY * (kWY + 1); e += blockDim.x) T[e / (kWY + 1)][e % (kWY + 1)] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    const double tj = tau[k0 + j];
+    double t = 0.0;
+    const int i = threadIdx.x;
+    if (i < j) {
+      for (int l = i; l < j; ++l) t += T[i][l] * G[l][j];
+    }
+    __syncthreads();
+    if (i < j) T[i][j] = -tj * t;
+    if (i == j) T[j][j] = tj;
+    __syncthreads();
+  }
+  // U_b[j][i] = sum_{l <= j} V[k0 + l][i] T[l][j], rows i > k0
+  double* Ub = U + int64_t(b) * kWY * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v[kWY];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-      y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    for (int l = 0; l < kWY; ++l) v[l] = (l < nb && i > k0) ? Vh[int64_t(k0 + l) * n + i] : 0.0;
+    // T is zero below its diagonal: the full sum over l is the triangular one
+#pragma unroll 1
+    for (int j = 0; j < kWY; ++j) {
+      double u = 0.0;
+#pragma unroll
+      for (int l = 0; l < kWY; ++l) u += v[l] * T[l][j];
+      Ub[int64_t(j) * n + i] = u;
     }
-    y0 *= tk;
-    y1 *= tk;
-    for (int i = k + 1 + lane; i < n; i += 32) {
-      const double vv = __ldg(vk + i);
-      z0[i] -= y0 * vv;
-      z1[i] -= y1 * vv;
-    }
-    __syncwarp();
   }
-  for (int i = lane; i < n; i += 32) {
-    g0[i] = z0[i];
-    if (two) g1[i] = z1[i];
+}
+
+// Z (cnt vectors, vector-major cnt x n) <- Q Z.  Cooperative: CTA p owns
+// rows [r0, r1) of every vector and keeps them in shared memory across the
+// blocks; per block it adds its rows' part of Y = V_b^T Z into Y_b (zeroed
+// beforehand, one slot per (vector group, block)), one grid barrier, then
+// updates its rows with U_b Y_b.
+__global__ void __launch_bounds__(256) wy_apply_kernel(const double* __restrict__ Vh, const double* __restrict__ U,
+                                                       int n, int nblk, int cnt, int chunk,
+                                                       double* __restrict__ Z, double* __restrict__ Y,
+                                                       unsigned* bar, int* status) {
+  extern __shared__ double wsm[];
+  double* Zs = wsm;                       // [kWYV][chunk]
+  double* Vs = Zs + kWYV * chunk;         // [kWY][chunk]
+  double* Us = Vs + kWY * chunk;          // [kWY][chunk]
+  double* Ys = Us + kWY * chunk;          // [kWY][kWYV]
+  const unsigned nb = gridDim.x;
+  const int r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  const int rows = max(0, r1 - r0);
+  const int ngroups = (cnt + kWYV - 1) / kWYV;
+  for (int g = 0; g < ngroups; ++g) {
+    const int vg = g * kWYV, nv = min(kWYV, cnt - vg);
+    for (int e = threadIdx.x; e < kWYV * chunk; e += blockDim.x) {
+      const int c = e / chunk, ri = e - c * chunk;
+      Zs[e] = (c < nv && ri < rows) ? Z[int64_t(vg + c) * n + r0 + ri] : 0.0;
+    }
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int k0 = b * kWY;
+      const int nbr = min(kWY, (n - 2) - k0);  // reflectors in this block (rows k0 .. k0 + nbr - 1 of Vh)
+      const int lo = max(0, k0 + 1 - r0);     // first local row with nonzero v (i > k0)
+      double* Yb = Y + (int64_t(g) * nblk + b) * kWY * kWYV;
+      __syncthreads();
+      if (lo < rows) {
+        for (int e = threadIdx.x; e < kWY * chunk; e += blockDim.x) {
+          const int j = e / chunk, ri = e - j * chunk;
+          const bool in = ri >= lo && ri < rows;
+          Vs[e] = in && j < nbr ? __ldg(Vh + int64_t(k0 + j) * n + r0 + ri) : 0.0;
+          Us[e] = in ? __ldg(U + (int64_t(b) * kWY + j) * n + r0 + ri) : 0.0;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kWY * nv; e += blockDim.x) {
+          const int j = e / nv, c = e - j * nv;
+          double s = 0.0;
+          for (int ri = lo; ri < rows; ++ri) s += Vs[j * chunk + ri] * Zs[c * chunk + ri];
+          atomicAdd(Yb + j * kWYV + c, s);
+        }
+      }
+      if (!grid_barrier(bar, nb, status)) return;
+      if (lo < rows) {
+        for (int e = threadIdx.x; e < kWY * nv; e += blockDim.x) {
+          const int j = e / nv, c = e - j * nv;
+          Ys[j * kWYV + c] = __ldcg(Yb + j * kWYV + c);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nv * rows; e += blockDim.x) {
+          const int c = e / rows, ri = e - c * rows;
+          if (ri < lo) continue;
+          double s = 0.0;
+#pragma unroll 8
+          for (int j = 0; j < kWY; ++j) s += Us[j * chunk + ri] * Ys[j * kWYV + c];
+          Zs[c * chunk + ri] -= s;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nv * chunk; e += blockDim.x) {
+      const int c = e / chunk, ri = e - c * chunk;
+      if (ri < rows) Z[int64_t(vg + c) * n + r0 + ri] = Zs[e];
+    }
   }
 }
 
@@ -485,9 +580,11 @@ __global__ void output_kernel(const double* __restrict__ Zc, int n, int cnt, dou
 constexpr int kInvBatch = 4096;
 
 struct EigScratch {
-  double *A, *Vh, *tau, *dv, *ev, *e2, *P, *info, *lam, *lamv, *u0, *u1, *u2, *Z, *Zc;
+  double *A, *Vh, *tau, *dv, *ev, *e2, *P, *info, *lam, *lamv, *u0, *u1, *u2, *Z, *Zc, *Uwy, *Ywy;
   size_t bytes;
 };
+
+int wy_blocks(int64_t d) { return d >= 3 ? int((d - 2 + kWY - 1) / kWY) : 0; }
 
 EigScratch carve_eig(void* base, int64_t d, int32_t nval, int32_t nvec) {
   Carve c(base);
@@ -508,6 +605,8 @@ EigScratch carve_eig(void* base, int64_t d, int32_t nval, int32_t nvec) {
   s.u2 = c.take<double>(d * B);
   s.Z = c.take<double>(d * B);
   s.Zc = c.take<double>(d * std::max(nvec, 1));
+  s.Uwy = c.take<double>(int64_t(wy_blocks(d)) * kWY * d);
+  s.Ywy = c.take<double>(int64_t((std::max(nvec, 1) + kWYV - 1) / kWYV) * wy_blocks(d) * kWY * kWYV);
   s.bytes = c.off + 256;
   return s;
 }
@@ -595,16 +694,41 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
       launches += 2;
     }
     cluster_mgs_kernel<<<unsigned(nvec), 256, 0, st>>>(lamv, nvec, s.info, 1e-7, n, s.Zc);
-    int wpb = int(std::min<int64_t>(4, std::max<int64_t>(1, (200 * 1024) / (int64_t(n) * 16))));
-    const size_t smem = size_t(wpb) * 2 * n * sizeof(double);
-    if ((e = cudaFuncSetAttribute(back_transform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(smem))) != cudaSuccess)
-      return e;
-    back_transform_kernel<<<unsigned((nvec + 2 * wpb - 1) / (2 * wpb)), wpb * 32, smem, st>>>(s.Vh, s.tau, n, nvec,
-                                                                                             s.Zc);
+    ++launches;
+    const int nblk = wy_blocks(n);
+    if (nblk > 0) {
+      // back-transformation Z <- Q Z in compact WY blocks
+      wy_prep_kernel<<<unsigned(nblk), 256, 0, st>>>(s.Vh, s.tau, n, s.Uwy);
+      const int ngroups = (nvec + kWYV - 1) / kWYV;
+      if ((e = cudaMemsetAsync(s.Ywy, 0, size_t(ngroups) * nblk * kWY * kWYV * sizeof(double), st)) != cudaSuccess)
+        return e;
+      if ((e = cudaMemsetAsync(h->d_barrier, 0, 64, st)) != cudaSuccess) return e;
+      int chunk = (n + h->num_sms - 1) / h->num_sms;
+      const int grid = (n + chunk - 1) / chunk;
+      const size_t smem = (size_t(kWYV + 2 * kWY) * chunk + size_t(kWY) * kWYV) * sizeof(double);
+      if ((e = cudaFuncSetAttribute(wy_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) !=
+          cudaSuccess)
+        return e;
+      int per_sm = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wy_apply_kernel, 256, smem)) != cudaSuccess)
+        return e;
+      if (per_sm < 1 || grid > per_sm * h->num_sms) return cudaErrorInvalidConfiguration;
+      const double* Vh = s.Vh;
+      const double* Uw = s.Uwy;
+      double* Z = s.Zc;
+      double* Y = s.Ywy;
+      unsigned* bar = h->d_barrier;
+      int* status = h->d_status;
+      int nn = n, nbk = nblk, nc = nvec, ch = chunk;
+      void* args[] = {&Vh, &Uw, &nn, &nbk, &nc, &ch, &Z, &Y, &bar, &status};
+      if ((e = cudaLaunchCooperativeKernel((void*)wy_apply_kernel, dim3(grid), dim3(256), args, smem, st)) !=
+          cudaSuccess)
+        return e;
+      launches += 2;
+    }
     dim3 b(32, 8), g(unsigned((nvec + 31) / 32), unsigned((n + 31) / 32));
     output_kernel<<<g, b, 0, st>>>(s.Zc, n, nvec, evecs, ldv);
-    launches += 3;
+    ++launches;
   }
   note_launch(launches);
   return cudaGetLastError();
