@@ -7,20 +7,22 @@
 //
 // Work item = (output tile 128 genes x 256 genes of the upper triangle,
 // K split: every nsplit-th drain block of the cells, so all CTAs sweep the
-// cells together and share each slice of the planes through L2).  The tensor core's FP32 accumulation is kept short:
-// the accumulator is drained every kSub K blocks (1024 cells) into an FP64
-// running tile owned by the CTA.  Its rounding error grows with the length
-// of a block (measured at 1M cells x 2000 genes against an FP64 Gram of the
-// same X: 3.7e-5 of max|S| with 2048-cell blocks, 1.85e-5 with 1024, 9.7e-6
-// with 512; the FP32 SIMT Gram reaches 3.2e-5); 1024 cells costs +20% time
-// over 2048, 512 cells +70%.  Persistent CTAs, warp-specialised:
+// cells together and share each slice of the planes through L2).  The tensor
+// core's FP32 accumulation is kept short: the accumulator is drained every
+// kSub K blocks (1024 cells) into a running tile owned by the CTA, kept as
+// double-float (FP32 hi + lo, exact TwoSum; ~2^-48 relative) so the drains
+// run on the FP32 pipe.  The accumulation's rounding error grows with the
+// length of a block (measured at 1M cells x 2000 genes against an FP64 Gram
+// of the same X: 3.7e-5 of max|S| with 2048-cell blocks, 1.85e-5 with 1024,
+// 9.7e-6 with 512; the FP32 SIMT Gram reaches 3.2e-5).  Persistent CTAs,
+// warp-specialised:
 //   warp 0      TMA producer: per K block the A (128 rows) and B (256 rows)
 //               slices of hi (and lo) into a 2-stage ring;
 //   warp 1      MMA issuer: tcgen05.mma M=128 N=256 K=16, FP32 accumulator
 //               in TMEM (double-buffered, 2 x 256 columns);
 //   warps 2-5   epilogue: tcgen05.ld each drained accumulator and add it to
-//               the item's FP64 tile; a second kernel sums the K splits in
-//               FP64 and writes both triangles of S.
+//               the item's running tile; a second kernel sums the K splits
+//               in FP64 and writes both triangles of S.
 // Every wait is bounded (GMGM_DEV_TIMEOUT on expiry, TMEM freed on exit).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -64,13 +66,24 @@ __device__ __forceinline__ void g_abort(GBars* bs, int* status) {
   set_status(status, GMGM_DEV_TIMEOUT);
 }
 
+// (hi, lo) += x in double-float: hi + lo carries the running sum to ~2^-48
+// relative (TwoSum: the rounding error of hi + x is exact in FP32), on the
+// FP32 pipe (GB300's FP64 rate would bound the drains).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += err;
+}
+
 // tiles: list of (row tile, col tile) of the upper triangle; nprod: 1 (BF16)
 // or 3 (3xBF16).
 __global__ void __launch_bounds__(kGThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                    const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                    const int2* __restrict__ tiles, int ntiles, int nkb_total, int nsplit, int nprod,
-                   double* __restrict__ part, int* __restrict__ status) {
+                   float2* __restrict__ part, int* __restrict__ status) {
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   GBars* bs = reinterpret_cast<GBars*>(smem + kGStages * kStageBytes);
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     long long accu = 0;
     for (int w = blockIdx.x; w < items && !g_aborted(bs); w += gridDim.x) {
       const int ch = w / ntiles;
-      double2* dst = reinterpret_cast<double2*>(part + (int64_t(w) * kGM + row) * kGN);
+      float4* dst = reinterpret_cast<float4*>(part + (int64_t(w) * kGM + row) * kGN);
       for (int sb = ch * kSub; sb < nkb_total && !g_aborted(bs); sb += kstride, ++accu) {
         const int b = int(accu & 1);
         if (!tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kGSpin)) {
@@ -191,11 +204,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
           tc::tmem_ld_wait();
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            double2 v = make_double2(double(__uint_as_float(r[2 * e])), double(__uint_as_float(r[2 * e + 1])));
-            if (!init) {
-              const double2 o = dst[c * 16 + e];
-              v.x += o.x;
-              v.y += o.y;
+            const float x0 = __uint_as_float(r[2 * e]), x1 = __uint_as_float(r[2 * e + 1]);
+            float4 v;  // (hi, lo) of two columns
+            if (init) {
+              v = make_float4(x0, 0.f, x1, 0.f);
+            } else {
+              v = dst[c * 16 + e];
+              two_sum_acc(v.x, v.y, x0);
+              two_sum_acc(v.z, v.w, x1);
             }
             dst[c * 16 + e] = v;
           }
@@ -213,8 +229,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
   }
 }
 
-// S[a][c] = sum over K splits of the partial tile holding (min, max) (FP64).
-__global__ void gram_tc_combine_kernel(const double* __restrict__ part, const int* __restrict__ tile_of, int ntn,
+// S[a][c] = sum over K splits of the partial tile holding (min, max), each a
+// double-float (hi, lo) pair, summed in FP64.
+__global__ void gram_tc_combine_kernel(const float2* __restrict__ part, const int* __restrict__ tile_of, int ntn,
                                        int ntiles, int nsplit, int64_t p, double* __restrict__ S, int64_t lds,
                                        int accumulate) {
   const int64_t a = int64_t(blockIdx.y) * blockDim.y + threadIdx.y;
@@ -224,7 +241,10 @@ __global__ void gram_tc_combine_kernel(const double* __restrict__ part, const in
   const int ti = tile_of[(lo / kGM) * ntn + hi / kGN];
   const int64_t off = (lo % kGM) * kGN + hi % kGN;
   double s = 0.0;
-  for (int ch = 0; ch < nsplit; ++ch) s += part[(int64_t(ch) * ntiles + ti) * (kGM * kGN) + off];
+  for (int ch = 0; ch < nsplit; ++ch) {
+    const float2 hl = part[(int64_t(ch) * ntiles + ti) * (kGM * kGN) + off];
+    s += double(hl.x) + double(hl.y);
+  }
   if (accumulate)
     S[a * lds + c] += s;
   else
@@ -294,7 +314,7 @@ cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec,
                            int accumulate, float* scratch, int /*splits*/) {
   GramPlan g = plan(m, h->num_sms);
   Carve c(scratch);
-  double* part = c.take<double>(size_t(g.nsplit) * g.ntiles * kGM * kGN);
+  float2* part = c.take<float2>(size_t(g.nsplit) * g.ntiles * kGM * kGN);
   int2* tiles = c.take<int2>(g.ntiles);
   int* tile_of = c.take<int>(size_t(g.ntm) * g.ntn);
   // tile list (host-built, small) and its inverse map
