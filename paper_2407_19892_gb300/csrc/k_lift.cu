@@ -25,7 +25,7 @@ __global__ void scale_w_kernel(const double* __restrict__ W, int64_t ldw, const 
 }
 
 template <int RC>
-__global__ void __launch_bounds__(kRows) lift_kernel(const float* __restrict__ x, int64_t n, int64_t p, int64_t ld,
+__global__ void __launch_bounds__(kRows, 2) lift_kernel(const float* __restrict__ x, int64_t n, int64_t p, int64_t ld,
                                                      const float* __restrict__ ws, int rpad, int c0, int r,
                                                      float* __restrict__ U, int64_t ldu) {
   __shared__ float xs[kG][kRows + 1];
