@@ -237,12 +237,13 @@ __device__ __forceinline__ int sturm_count(const double* dv, const double* e2, i
   return cnt;
 }
 
-constexpr int kMS = 8;  // lanes per eigenvalue (9-way multisection)
+constexpr int kBisectLanes = 8;  // lanes per eigenvalue ((lanes + 1)-way multisection)
 
 // Lanes in groups of kMS find the ascending eigenvalues j0 + group (or
 // jlist[group]): each round evaluates kMS interior points of the current
 // interval and keeps the sub-interval holding eigenvalue j (counts are
 // monotone in x).
+template <int kMS>
 __global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __restrict__ e2_g, int n, int j0,
                               const int* __restrict__ jlist, int cnt, const double* __restrict__ info,
                               double* __restrict__ lam) {
@@ -268,7 +269,8 @@ __global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __r
     const double x = lo + (hi - lo) * double(sub + 1) / double(kMS + 1);
     const int c = sturm_count(dv, e2, n, x);
     const unsigned bal = __ballot_sync(0xffffffffu, c <= j);
-    const int t = __popc((bal >> gbase) & ((1u << kMS) - 1));  // points with count <= j (a prefix)
+    const unsigned gmask = kMS == 32 ? 0xffffffffu : ((1u << (kMS & 31)) - 1u);
+    const int t = __popc((bal >> gbase) & gmask);  // points with count <= j (a prefix)
     const double xl = __shfl_sync(0xffffffffu, x, gbase + (t > 0 ? t - 1 : 0));
     const double xh = __shfl_sync(0xffffffffu, x, gbase + (t < kMS ? t : kMS - 1));
     if (!done) {
@@ -661,14 +663,14 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
   tri_info_kernel<<<1, 256, 0, st>>>(s.dv, s.ev, n, s.e2, s.info);
   launches += 2;
   const size_t bsmem = size_t(2) * n * sizeof(double);
-  if ((e = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bsmem))) !=
-      cudaSuccess)
+  if ((e = cudaFuncSetAttribute(bisect_kernel<kBisectLanes>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(bsmem))) != cudaSuccess)
     return e;
-  const int tpb = 64;  // small blocks: the groups spread over every SM
+  const int tpb = kBisectLanes >= 8 ? 64 : 32;  // small blocks: the groups spread over every SM
   if (nval > 0) {
     // the nval largest eigenvalues, ascending in lam
-    const int64_t threads = int64_t(nval) * kMS;
-    bisect_kernel<<<unsigned((threads + tpb - 1) / tpb), tpb, bsmem, st>>>(s.dv, s.e2, n, n - nval, nullptr, nval,
+    const int64_t threads = int64_t(nval) * kBisectLanes;
+    bisect_kernel<kBisectLanes><<<unsigned((threads + tpb - 1) / tpb), tpb, bsmem, st>>>(s.dv, s.e2, n, n - nval, nullptr, nval,
                                                                           s.info, s.lam);
     values_kernel<<<unsigned((nval + 255) / 256), 256, 0, st>>>(s.lam, nval, evals);
     launches += 2;
@@ -678,8 +680,8 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
     // ascending indices
     const double* lamv = s.lam + (nval - nvec);
     if (vlist || nvec > nval) {
-      const int64_t threads = int64_t(nvec) * kMS;
-      bisect_kernel<<<unsigned((threads + tpb - 1) / tpb), tpb, bsmem, st>>>(s.dv, s.e2, n, n - nvec, vlist, nvec,
+      const int64_t threads = int64_t(nvec) * kBisectLanes;
+      bisect_kernel<kBisectLanes><<<unsigned((threads + tpb - 1) / tpb), tpb, bsmem, st>>>(s.dv, s.e2, n, n - nvec, vlist, nvec,
                                                                             s.info, s.lamv);
       lamv = s.lamv;
       ++launches;
