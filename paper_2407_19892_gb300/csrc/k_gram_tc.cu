@@ -47,6 +47,7 @@ constexpr int kABytes = kGM * 128;           // 16 KB per plane
 constexpr int kBBytes = kGN * 128;           // 32 KB per plane
 constexpr int kStageBytes = 2 * (kABytes + kBBytes);
 constexpr long long kGSpin = 1ll << 23;
+constexpr int kPaceWindow = 2;               // drains a CTA may run ahead of the slowest
 
 struct __align__(8) GBars {
   uint64_t full[kGStages];
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                    const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                    const int2* __restrict__ tiles, int ntiles, int nkb_total, int nsplit, int nprod,
-                   float2* __restrict__ part, int* __restrict__ status) {
+                   float2* __restrict__ part, unsigned* __restrict__ pace, int* __restrict__ status) {
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   GBars* bs = reinterpret_cast<GBars*>(smem + kGStages * kStageBytes);
@@ -113,6 +114,25 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const int ch = w / ntiles, ti = w - ch * ntiles;
         const int2 tl = tiles[ti];
         for (int sb = ch * kSub; sb < nkb_total && !g_aborted(bs); sb += kstride) {
+          if (pace) {
+            // pacing (one item per co-resident CTA): start drain q once every
+            // CTA has started drain q - kPaceWindow, so the CTAs sweep the
+            // cells within an L2-sized window and share the planes' reads
+            const int q = (sb - ch * kSub) / kstride;
+            atomicAdd(pace + q, 1u);
+            if (q >= kPaceWindow) {
+              const volatile unsigned* pw = pace + (q - kPaceWindow);
+              long long spins = 0;
+              while (*pw < gridDim.x) {
+                if (g_aborted(bs) || ++spins > kGSpin) {
+                  g_abort(bs, status);
+                  break;
+                }
+                __nanosleep(64);
+              }
+              if (g_aborted(bs)) break;
+            }
+          }
           const int se = min(nkb_total, sb + kSub);
           for (int kb = sb; kb < se; ++kb, ++issued) {
             const int s = int(issued % kGStages);
@@ -307,7 +327,7 @@ int gram_tc_splits(gmgm_handle* h, const gmgm_matrix* m) { return plan(m, h->num
 size_t gram_tc_scratch_bytes(gmgm_handle* h, const gmgm_matrix* m) {
   GramPlan g = plan(m, h->num_sms);
   return Carve::round(size_t(g.nsplit) * g.ntiles * kGM * kGN * 8) + Carve::round(size_t(g.ntiles) * 8) +
-         Carve::round(size_t(g.ntm) * g.ntn * 4) + 4096;
+         Carve::round(size_t(g.ntm) * g.ntn * 4) + Carve::round((size_t(g.nkb) + 2) * 4) + 4096;
 }
 
 cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec, double* S, int64_t lds,
@@ -317,6 +337,7 @@ cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec,
   float2* part = c.take<float2>(size_t(g.nsplit) * g.ntiles * kGM * kGN);
   int2* tiles = c.take<int2>(g.ntiles);
   int* tile_of = c.take<int>(size_t(g.ntm) * g.ntn);
+  unsigned* pace = c.take<unsigned>(size_t(g.nkb) + 2);
   // tile list (host-built, small) and its inverse map
   std::vector<int2> ht;
   std::vector<int> hof(size_t(g.ntm) * g.ntn, -1);
@@ -346,8 +367,25 @@ cudaError_t launch_gram_tc(gmgm_handle* h, const gmgm_matrix* m, gmgm_prec prec,
     return e;
   const int items = g.ntiles * g.nsplit;
   const int grid = std::min(items, h->num_sms);
-  gram_tc_kernel<<<grid, kGThreads, kGSmem, h->stream>>>(ah, al, bh, bl, tiles, g.ntiles, g.nkb, g.nsplit, nprod,
-                                                         part, h->d_status);
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_tc_kernel, kGThreads, kGSmem)) != cudaSuccess)
+    return e;
+  if (items <= h->num_sms && per_sm >= 1) {
+    // one item per CTA, all co-resident (cooperative launch): paced sweep
+    const int kstride = g.nsplit * kSub;
+    const int nq = (g.nkb + kstride - 1) / kstride + 1;
+    if ((e = cudaMemsetAsync(pace, 0, size_t(nq) * sizeof(unsigned), h->stream)) != cudaSuccess) return e;
+    const int2* tl = tiles;
+    int nt = g.ntiles, nkb = g.nkb, ns = g.nsplit, np = nprod;
+    int* status = h->d_status;
+    void* args[] = {&ah, &al, &bh, &bl, &tl, &nt, &nkb, &ns, &np, &part, &pace, &status};
+    if ((e = cudaLaunchCooperativeKernel((void*)gram_tc_kernel, dim3(grid), dim3(kGThreads), args, kGSmem,
+                                         h->stream)) != cudaSuccess)
+      return e;
+  } else {
+    gram_tc_kernel<<<grid, kGThreads, kGSmem, h->stream>>>(ah, al, bh, bl, tiles, g.ntiles, g.nkb, g.nsplit, nprod,
+                                                           part, nullptr, h->d_status);
+  }
   dim3 cb(32, 8), cg(unsigned((m->cols + 31) / 32), unsigned((m->cols + 7) / 8));
   gram_tc_combine_kernel<<<cg, cb, 0, h->stream>>>(part, tile_of, g.ntn, g.ntiles, g.nsplit, m->cols, S, lds,
                                                    accumulate);
