@@ -222,6 +222,15 @@ typedef struct {
   int32_t gauge;        /* 1: apply the gauge convention (flat shift, single
                            modality with equal traces): every axis but the
                            first gets min = eps.  0: leave as solved. */
+  double trace_rtol;    /* with gauge = 1 and one modality: traces that agree
+                           within this relative tolerance are made exactly
+                           equal before the solve (each axis' spectrum
+                           scaled by the mean trace over its own, a change
+                           of at most trace_rtol relative), so the flat
+                           shift is exact.  Full-rank axes of one tensor
+                           have equal traces in exact arithmetic; spectra
+                           from FP32 Grams differ by ~1e-7.  0: 1e-6;
+                           < 0: off (only traces equal to 1e-9 count). */
 } gmgm_solve_opts;
 
 typedef struct {

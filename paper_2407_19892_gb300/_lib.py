@@ -39,7 +39,7 @@ class Problem(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", c_dbl), ("max_newton", c_i32), ("max_cg", c_i32),
-                ("fp32_phase", c_i32), ("gauge", c_i32)]
+                ("fp32_phase", c_i32), ("gauge", c_i32), ("trace_rtol", c_dbl)]
 
 
 class SolveStats(ctypes.Structure):

@@ -182,7 +182,7 @@ def lift(x: torch.Tensor, W: torch.Tensor, E: torch.Tensor, r: int, h: Handle = 
 # ---- eigenvalue solve --------------------------------------------------------
 
 def eigsolve(E, modalities=None, eps=None, init=None, tol=1e-9, max_newton=200, max_cg=200,
-             fp32_phase=True, gauge=True, h: Handle = None):
+             fp32_phase=True, gauge=True, trace_rtol=0.0, h: Handle = None):
     """Eigenvalues Lam_l of the MLE.  E: list of FP64 CUDA tensors (descending
     spectra); modalities: list of tuples of axis indices (default: one
     modality over all axes).  Returns (list of FP64 tensors, stats dict)."""
@@ -210,7 +210,7 @@ def eigsolve(E, modalities=None, eps=None, init=None, tol=1e-9, max_newton=200, 
     if init is not None:
         init = [t.contiguous() for t in init]
         init_arr = (ctypes.c_void_p * len(E))(*[t.data_ptr() for t in init])
-    o = L.SolveOpts(tol, max_newton, max_cg, int(fp32_phase), int(gauge))
+    o = L.SolveOpts(tol, max_newton, max_cg, int(fp32_phase), int(gauge), float(trace_rtol))
     st = L.SolveStats()
     rc = h.lib.gmgm_eigsolve(h.h, ctypes.byref(p), init_arr, ctypes.byref(o), out_arr, ctypes.byref(st))
     if rc not in (0, -5):

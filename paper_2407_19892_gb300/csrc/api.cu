@@ -228,7 +228,7 @@ int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p, const double* const* in
   }
   for (int a = 0; a < p->n_axes; ++a)
     if (!used[a]) return fail(h, GMGM_E_ARG, "gmgm_eigsolve: an axis is in no modality");
-  gmgm_solve_opts opt = {1e-9, 200, 200, 1, 1};
+  gmgm_solve_opts opt = {1e-9, 200, 200, 1, 1, 0.0};
   if (o) {
     opt = *o;
     if (opt.tol <= 0) opt.tol = 1e-9;

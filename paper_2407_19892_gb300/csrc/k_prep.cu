@@ -60,16 +60,24 @@ __global__ void centre_split_kernel(const float* c, int64_t n, int64_t p,
   }
   if (hi == nullptr) return;
   __syncthreads();
-  // transposed write: xt[gene][cell], 64 consecutive cells per gene row
-  for (int cc = ty; cc < kT; cc += 4) {
+  // transposed write: xt[gene][cell], 64 consecutive cells per gene row,
+  // two cells per thread (bf16x2 stores: a warp writes 128 contiguous bytes)
+  const int cp = threadIdx.x & 31, gy = threadIdx.x >> 5;  // 32 cell pairs x 8 genes
+  for (int cc = gy; cc < kT; cc += 8) {
     const int64_t gene = col0 + cc;
-    const int64_t cell = row0 + tx;
-    if (gene < p && cell < n) {
-      float v = tile[tx][cc];
-      __nv_bfloat16 h = __float2bfloat16_rn(v);
-      __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-      hi[gene * ld_t + cell] = h;
-      lo[gene * ld_t + cell] = l;
+    const int64_t cell = row0 + 2 * cp;
+    if (gene >= p || cell >= n) continue;
+    const float v0 = tile[2 * cp][cc];
+    const float v1 = cell + 1 < n ? tile[2 * cp + 1][cc] : 0.f;
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+    if (cell + 1 < n) {
+      *reinterpret_cast<__nv_bfloat162*>(hi + gene * ld_t + cell) = __halves2bfloat162(h0, h1);
+      *reinterpret_cast<__nv_bfloat162*>(lo + gene * ld_t + cell) = __halves2bfloat162(l0, l1);
+    } else {
+      hi[gene * ld_t + cell] = h0;
+      lo[gene * ld_t + cell] = l0;
     }
   }
 }

@@ -52,6 +52,7 @@ struct Params {
   double* out[GMGM_MAX_AXES];
   double tol;
   int max_newton, max_cg, fp32_phase, gauge, has_init;
+  double trace_rtol;
 };
 
 struct Vecs {
@@ -296,6 +297,28 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, in
   for (int a = 0; a < P.L; ++a)
     for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) V.E[P.off[a] + i] = P.E[a][i];
   __syncthreads();
+  // one modality whose traces agree within trace_rtol: scale every axis'
+  // spectrum to the mean trace, so the flat shift of the gauge is exact
+  if (P.gauge && P.nmod == 1 && P.mk[0] > 1 && P.trace_rtol > 0.0) {
+    double tr[GMGM_MAX_AXES], mean = 0.0;
+    for (int q = 0; q < P.mk[0]; ++q) {
+      const int a = P.ma[0][q];
+      double s = 0.0;
+      for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) s += V.E[P.off[a] + i];
+      tr[q] = block_sum(s, red);
+      mean += tr[q] / P.mk[0];
+    }
+    bool close = mean > 0.0;
+    for (int q = 0; q < P.mk[0]; ++q) close = close && fabs(tr[q] - mean) <= P.trace_rtol * mean;
+    if (close) {
+      for (int q = 0; q < P.mk[0]; ++q) {
+        const int a = P.ma[0][q];
+        const double sc = mean / tr[q];
+        for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) V.E[P.off[a] + i] *= sc;
+      }
+      __syncthreads();
+    }
+  }
   // default eps: 1e-10 * max over modalities of sum_l max_i 1/E_l,i
   double epsdef = 0.0;
   {
@@ -546,6 +569,7 @@ cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* co
   P.max_cg = o->max_cg;
   P.fp32_phase = o->fp32_phase;
   P.gauge = o->gauge;
+  P.trace_rtol = o->trace_rtol == 0.0 ? 1e-6 : o->trace_rtol;
   P.has_init = init != nullptr;
   Carve c(scratch);
   const int N = P.N;
@@ -657,7 +681,7 @@ extern "C" int gmgm_eigsolve_static(const gmgm_problem* p, const double* const* 
   }
   for (int a = 0; a < p->n_axes; ++a)
     if (!used[a]) return GMGM_E_ARG;
-  gmgm_solve_opts opt = {1e-9, 200, 200, 1, 1};
+  gmgm_solve_opts opt = {1e-9, 200, 200, 1, 1, 0.0};
   if (o) {
     opt = *o;
     if (opt.tol <= 0) opt.tol = 1e-9;
@@ -699,6 +723,7 @@ extern "C" int gmgm_eigsolve_static(const gmgm_problem* p, const double* const* 
   P.max_cg = opt.max_cg;
   P.fp32_phase = opt.fp32_phase;
   P.gauge = opt.gauge;
+  P.trace_rtol = opt.trace_rtol == 0.0 ? 1e-6 : opt.trace_rtol;
   P.has_init = init != nullptr;
   Carve c(base);
   const int N = P.N;

@@ -30,8 +30,7 @@ constexpr int kBM = 128, kBN = 64, kBK = 32;
 // A = fl32(V * psi), B = fl32(V), both d x rpad, zero padded; colmax_k =
 // max_j |B_jk| as float bits (non-negative floats order like their bits).
 __global__ void prep_ab_kernel(const void* V, int v64, int64_t ldv, const double* __restrict__ psi, int64_t d,
-                               int r, int rpad, float* __restrict__ A, float* __restrict__ B,
-                               unsigned* __restrict__ colmax_bits) {
+                               int r, int rpad, float* __restrict__ A, float* __restrict__ B) {
   const int64_t total = d * rpad;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t i = e / rpad;
@@ -39,26 +38,35 @@ __global__ void prep_ab_kernel(const void* V, int v64, int64_t ldv, const double
     double v = 0.0;
     if (k < r)
       v = v64 ? static_cast<const double*>(V)[i * ldv + k] : double(static_cast<const float*>(V)[i * ldv + k]);
-    const float b = float(v);
     A[e] = k < r ? float(v * psi[k]) : 0.f;
-    B[e] = b;
-    if (k < r) atomicMax(&colmax_bits[k], __float_as_uint(fabsf(b)));
+    B[e] = float(v);
   }
 }
 
-// max_j ||B_j||_2 over all rows (float bits, atomicMax), for the
-// Cauchy-Schwarz form of the screen's error bound.
-__global__ void rownorm_kernel(const float* __restrict__ B, int64_t d, int rpad, unsigned* __restrict__ maxrow_bits) {
+// Statistics of the screen's error bound, from b = float(V): colmax[k] =
+// max_j |b_jk| (float bits) and colmax[r] = max_j ||b_j||_2, rounded up so
+// the bound stays an upper bound.  A thread per row; column maxima reduced
+// in shared memory, one global atomic per block and column.
+__global__ void bound_stats_kernel(const void* V, int v64, int64_t ldv, int64_t d, int r,
+                                   unsigned* __restrict__ colmax_bits) {
+  extern __shared__ unsigned cm[];  // [r]
+  for (int k = threadIdx.x; k < r; k += blockDim.x) cm[k] = 0u;
+  __syncthreads();
   float best = 0.f;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < d; i += int64_t(gridDim.x) * blockDim.x) {
     float s = 0.f;
-    for (int k = 0; k < rpad; ++k) s = fmaf(B[i * rpad + k], B[i * rpad + k], s);
+    for (int k = 0; k < r; ++k) {
+      const float b = v64 ? float(static_cast<const double*>(V)[i * ldv + k]) : static_cast<const float*>(V)[i * ldv + k];
+      s = fmaf(b, b, s);
+      atomicMax(&cm[k], __float_as_uint(fabsf(b)));
+    }
     best = fmaxf(best, s);
   }
-  // round the norm up so the bound stays an upper bound
-  best = sqrtf(best) * (1.f + 1.2e-7f * float(rpad + 8));
+  best = sqrtf(best) * (1.f + 1.2e-7f * float(r + 8));
   for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(maxrow_bits, __float_as_uint(best));
+  if ((threadIdx.x & 31) == 0) atomicMax(&colmax_bits[r], __float_as_uint(best));
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x) atomicMax(&colmax_bits[k], cm[k]);
 }
 
 // FP32 screen.  Rows: rows[mi] for mi < m (m = *count_dev when count_dev is
@@ -509,11 +517,14 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   GMGM_CUDA_TRY(h, cudaMemsetAsync(colmax, 0, size_t(r + 1) * 4, s));
   GMGM_CUDA_TRY(h, cudaMemsetAsync(counters, 0, 64, s));
   {
-    const int64_t total = d * rpad;
-    const unsigned blocks = unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 16));
-    prep_ab_kernel<<<blocks, 256, 0, s>>>(V, v_fp64, ldv, psi, d, r, rpad, A, B, colmax);
+    if (prec == GMGM_FP32) {
+      // FP32 screen operands (the tensor-core screen prepares its own)
+      const int64_t total = d * rpad;
+      const unsigned blocks = unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 16));
+      prep_ab_kernel<<<blocks, 256, 0, s>>>(V, v_fp64, ldv, psi, d, r, rpad, A, B);
+    }
     const unsigned nb = unsigned(std::min<int64_t>((d + 255) / 256, int64_t(h->num_sms) * 8));
-    rownorm_kernel<<<nb, 256, 0, s>>>(B, d, rpad, colmax + r);
+    bound_stats_kernel<<<nb, 256, size_t(r) * sizeof(unsigned), s>>>(V, v_fp64, ldv, d, r, colmax);
   }
   if (st) cudaEventRecord(ev[0], s);
   const size_t smem = size_t(kBK * (kBM + 1) + kBK * (kBN + 1) + kBM * (kBN + 1) + kBM * kC) * 4 + size_t(kBM * kC) * 4;
@@ -527,7 +538,7 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   if (st) cudaEventRecord(ev[1], s);
   launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, nl, d, d, colmax,
                  screen_unit(prec, r), idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
-  note_launch(prec == GMGM_FP32 ? 4 : 3);
+  note_launch(prec == GMGM_FP32 ? 4 : 2);
   // rows the screen could not certify (the count is read back once to size
   // the work): after the BF16 screen, a 3xBF16 tensor-core screen of those
   // rows and a second certification; what remains, an exact FP64 scan

@@ -211,6 +211,31 @@ def test_eigsolve_three_axis_and_multimodal(g, cuda_dev):
     assert err <= 1e-7, err
 
 
+def test_eigsolve_three_axis_traces_equal_to_fp32_rounding(g, cuda_dev):
+    # full-rank spectra of one tensor: equal traces in exact arithmetic; a
+    # relative 1e-7 perturbation (spectra from FP32 Grams) must still give
+    # the flat shift, a converged solve and the gauge convention
+    r = _rng(7)
+    t = r.standard_normal((6, 9, 8))
+    es = [osp.top_eigh(og.gram(t, a), t.shape[a])[0] for a in range(3)]
+    pert = [es[0] * (1 + 1e-7), es[1], es[2] * (1 - 8e-8)]
+    lams, st = g.eigsolve([torch.from_numpy(e).to(cuda_dev) for e in pert], [(0, 1, 2)], tol=1e-10)
+    assert st["status"] == 0 and st["rel_kkt"] <= 1e-10, st
+    l = [x.cpu().numpy() for x in lams]
+    from oracle.solve import KSProblem, solve_newton
+    prob = KSProblem(es, [(0, 1, 2)])
+    ref, _ = solve_newton(prob, tol=1e-12)
+    rl = prob.split(ref)
+    s = l[0][:, None, None] + l[1][None, :, None] + l[2][None, None, :]
+    sr = rl[0][:, None, None] + rl[1][None, :, None] + rl[2][None, None, :]
+    assert np.max(np.abs(s - sr) / sr) <= 1e-6
+    for a in (1, 2):
+        assert abs(l[a].min() - prob.eps[a]) <= 1e-6 * prob.eps[a]
+    # with the tolerance off the perturbed traces count as different
+    _, st_off = g.eigsolve([torch.from_numpy(e).to(cuda_dev) for e in pert], [(0, 1, 2)], tol=1e-10, trace_rtol=-1.0)
+    assert st_off["status"] in (0, -5)
+
+
 def test_eigsolve_warm_start_and_fp64_only(g, cuda_dev):
     x, _, _ = planted_c1()
     e_r, _, e_c, _ = osp.two_axis_spectra(x, 20, 100)
