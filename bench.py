@@ -338,24 +338,45 @@ def main():
     unc = int(res.topk_rows_stats["rows_uncertified"])
 
     # ---- end to end through the public API with host buffers ----
+    # Every step copies its input (8 GB of counts) from pinned host memory
+    # and reads its networks back.  Inputs stream through two device buffers
+    # on a copy stream, so step i + 1's copy overlaps step i's kernels (what
+    # a user streaming datasets through the library does); the first copy is
+    # inside the timed region, and each result is read back after its step.
     e2e = None
     if not a.no_e2e:
         host = counts.cpu().pin_memory()
-        dev_in = torch.empty_like(counts)
+        bufs = [torch.empty_like(counts), torch.empty_like(counts)]
         idx_h = torch.empty(a.cells, a.k_cells, dtype=torch.int32).pin_memory()
         val_h = torch.empty(a.cells, a.k_cells, dtype=torch.float32).pin_memory()
         gidx_h = torch.empty(a.genes, a.k_genes, dtype=torch.int32).pin_memory()
         gval_h = torch.empty(a.genes, a.k_genes, dtype=torch.float32).pin_memory()
-        n_e2e = a.e2e_steps or a.steps
-        dev_in.copy_(host, non_blocking=True)
-        step(dev_in)
+        n_e2e = a.e2e_steps or max(a.steps, 6)
+        copy_stream = torch.cuda.Stream(dev)
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        free = [torch.cuda.Event(), torch.cuda.Event()]
+        bufs[0].copy_(host, non_blocking=True)
+        step(bufs[0])
         barrier()
         q0 = torch.cuda.Event(enable_timing=True)
         q1 = torch.cuda.Event(enable_timing=True)
         q0.record(stream)
-        for _ in range(n_e2e):
-            dev_in.copy_(host, non_blocking=True)
-            r2 = step(dev_in)
+        copy_stream.wait_event(q0)
+        with torch.cuda.stream(copy_stream):
+            bufs[0].copy_(host, non_blocking=True)
+        ready[0].record(copy_stream)
+        for i in range(n_e2e):
+            b = i % 2
+            stream.wait_event(ready[b])
+            if i + 1 < n_e2e:
+                nb = (i + 1) % 2
+                if i >= 1:
+                    copy_stream.wait_event(free[nb])  # step i - 1 is done with that buffer
+                with torch.cuda.stream(copy_stream):
+                    bufs[nb].copy_(host, non_blocking=True)
+                ready[nb].record(copy_stream)
+            r2 = step(bufs[b])
+            free[b].record(stream)
             idx_h.copy_(r2.idx_rows, non_blocking=True)
             val_h.copy_(r2.val_rows, non_blocking=True)
             gidx_h.copy_(r2.idx_cols, non_blocking=True)
@@ -365,8 +386,9 @@ def main():
         ems = replicas.max_over_ranks(q0.elapsed_time(q1) / n_e2e, dev)
         e2e = {"value": replicas.job_throughput(a.cells, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": host.numel() * 4,
-               "d2h_bytes_per_step": (idx_h.numel() + val_h.numel() + gidx_h.numel() + gval_h.numel()) * 4}
-        del host, dev_in
+               "d2h_bytes_per_step": (idx_h.numel() + val_h.numel() + gidx_h.numel() + gval_h.numel()) * 4,
+               "steps": n_e2e, "input_copies": "overlapped with the previous step (two device buffers)"}
+        del host, bufs
 
     # ---- the plain FP32 form (SIMT Gram and screen), one step, for comparison ----
     fp32_form = None
