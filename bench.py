@@ -202,6 +202,11 @@ def peaks():
 
 # ---------------------------------------------------------------------------
 
+def workload_name(a):
+    return (f"two-axis fit, {a.cells} cells x {a.genes} genes (scRNA-like NB counts, {a.clusters} clusters), "
+            f"r_cells={a.r_cells}, full gene spectrum, k_cells={a.k_cells}, k_genes={a.k_genes}")
+
+
 def reference_arm(a, world, rank):
     """The oracle as it stands, on the host cores: each step fits a bounded
     sample of the workload and extrapolates to the full one."""
@@ -224,8 +229,7 @@ def reference_arm(a, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"two-axis fit, {a.cells} cells x {a.genes} genes, r_cells={a.r_cells}, "
-                               f"k_cells={a.k_cells}, k_genes={a.k_genes}", "cells": a.cells, "genes": a.genes},
+        "config": {"workload": workload_name(a), "cells": a.cells, "genes": a.genes, "parallelism": "host cores"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": blas_threads() or cpu_cores(), "kind": "oracle",
                          "sample": f"{n_s} cells (cell top-k on {max(100, a.cpu_sample_rows // 4)} rows), "
                                    f"stages extrapolated to {a.cells} cells by complexity"},
@@ -445,9 +449,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": dtype, "data": "synthetic",
-        "config": {"workload": f"two-axis fit, {a.cells} cells x {a.genes} genes (scRNA-like NB counts, "
-                               f"{a.clusters} clusters), r_cells={a.r_cells}, full gene spectrum, "
-                               f"k_cells={a.k_cells}, k_genes={a.k_genes}",
+        "config": {"workload": workload_name(a),
                    "cells": a.cells, "genes": a.genes, "gram_prec": a.gram_prec, "topk_prec": a.topk_prec,
                    "l2": "inputs larger than L2 (8 GB counts per step)", "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
