@@ -96,6 +96,10 @@ def method_problem(seed, device, cells=None, genes=None, r_cells=None, cell_rang
     rng = np.random.default_rng(seed)
     cells = cells or int(np.exp(rng.uniform(np.log(cell_range[0]), np.log(cell_range[1]))))
     genes = genes or int(np.exp(rng.uniform(np.log(gene_range[0]), np.log(gene_range[1]))))
+    # the full gene spectrum needs X of full column rank: at least twice as
+    # many cells as genes (with fewer cells most gene eigenvalues are zero
+    # and the box problem has no bounded optimum)
+    genes = min(genes, cells // 2)
     r_cells = r_cells or int(rng.integers(8, min(100, genes // 2)))
     clusters = int(rng.integers(4, 40))
     counts = scrna_counts(cells, genes, clusters, seed=int(seed), device=device)
@@ -105,14 +109,21 @@ def method_problem(seed, device, cells=None, genes=None, r_cells=None, cell_rang
     return e[:r_cells].contiguous(), e.contiguous()
 
 
-def method_pairs(n, seed=0, device="cuda", tol=1e-9, **ranges):
-    """n (features, targets) pairs: the method's own cold-start solutions of
-    seeded synthetic problems."""
+def method_pairs(n, seed=0, device="cuda", tol=1e-9, deadline=None, skipped=None, **ranges):
+    """Up to n (features, targets) pairs: the method's own cold-start
+    solutions of seeded synthetic problems (stops early at `deadline`, a
+    time.time() value, if given).  Problems whose solve did not reach `tol`
+    are left out (and listed in `skipped` if a list is given)."""
+    import time
     F, T = [], []
     for i in range(n):
+        if deadline is not None and time.time() > deadline:
+            break
         e0, e1 = method_problem(seed * 100003 + i, device, **ranges)
         (l0, l1), st = eigsolve([e0, e1], [(0, 1)], tol=tol)
         if st["status"] != 0:
+            if skipped is not None:
+                skipped.append({"problem": i, "cells_rank": int(e0.numel()), "genes": int(e1.numel()), **st})
             continue
         F.append(features(e0, e1))
         T.append(targets(e0, e1, l0, l1))

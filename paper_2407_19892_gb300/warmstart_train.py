@@ -3,10 +3,10 @@
     python -m paper_2407_19892_gb300.warmstart_train [--problems 800] [--steps 6000]
 
 Training pairs are generated by the method itself: seeded scRNA-like count
-matrices (log-uniform 1k-50k cells x 200-2000 genes, random cluster counts and
-cell ranks) go through the GPU preprocessing, Gram, FP64 spectra and the
-cold-start eigenvalue solve; the network learns solved eigenvalues from
-spectra.  Forward, backward and Adam run in the library's kernels.  Writes
+matrices (log-uniform 1k-200k cells x 500-5000 genes by default, random
+cluster counts and cell ranks) go through the GPU preprocessing, Gram, FP64
+spectra and the cold-start eigenvalue solve; the network learns solved
+eigenvalues from spectra.  Forward, backward and Adam run in the library's kernels.  Writes
 ``warmstart_mlp.npz`` next to this file.
 """
 
@@ -21,7 +21,10 @@ from . import build, warmstart
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--problems", type=int, default=800)
+    ap.add_argument("--problems", type=int, default=5000)
+    ap.add_argument("--cells", type=int, nargs=2, default=(1000, 200000), help="log-uniform range of cells")
+    ap.add_argument("--genes", type=int, nargs=2, default=(500, 5000), help="log-uniform range of genes")
+    ap.add_argument("--max-minutes", type=float, default=None, help="stop generating problems after this long")
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -31,8 +34,9 @@ def main():
     build.build()
     dev = torch.device("cuda:0")
     t0 = time.time()
-    F, T = warmstart.method_pairs(a.problems, seed=a.seed, device=dev, cell_range=(1000, 50000),
-                                  gene_range=(200, 2000))
+    deadline = t0 + 60.0 * a.max_minutes if a.max_minutes else None
+    F, T = warmstart.method_pairs(a.problems, seed=a.seed, device=dev, cell_range=tuple(a.cells),
+                                  gene_range=tuple(a.genes), deadline=deadline)
     t1 = time.time()
     p = warmstart.init_params(a.seed, dev)
     loss0, _ = warmstart.loss_grad(p, F, T)
@@ -44,7 +48,8 @@ def main():
     loss1, _ = warmstart.loss_grad(p, F, T)
     torch.cuda.synchronize()
     warmstart.save(p, a.out)
-    print(json.dumps({"pairs": int(F.shape[0]), "gen_s": round(t1 - t0, 1), "train_s": round(time.time() - t1, 1),
+    print(json.dumps({"pairs": int(F.shape[0]), "cells": list(a.cells), "genes": list(a.genes),
+                      "gen_s": round(t1 - t0, 1), "train_s": round(time.time() - t1, 1),
                       "loss_initial": loss0, "loss_final": loss1, "out": a.out}))
 
 
