@@ -256,6 +256,10 @@ typedef struct {
  *   stats       host, optional; if non-NULL the call synchronises and fills
  *               it (and returns its status).
  * Sizes: sum_l r_l <= 16384; every modality grid <= 2^31 points.
+ * Every E_l,i must be positive and finite (f has no minimiser when some
+ * E_l,i <= 0, i.e. X lacks full rank on that axis): otherwise lambda_out is
+ * NaN, no iteration runs and the status is GMGM_E_INFEASIBLE (a zero or
+ * negative value) or GMGM_E_NONFINITE (a NaN or Inf).
  * Errors: GMGM_E_ARG; device bits NOT_CONVERGED / INFEASIBLE / NONFINITE. */
 int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p,
                   const double* const* init, const gmgm_solve_opts* opts,

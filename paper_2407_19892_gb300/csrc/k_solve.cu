@@ -294,9 +294,37 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, in
   if (threadIdx.x == 0) bad_s = 0;
   const int N = P.N;
   // ---- setup: E, box, start ----
+  int bad_e = 0, nonfinite_e = 0;
   for (int a = 0; a < P.L; ++a)
-    for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) V.E[P.off[a] + i] = P.E[a][i];
-  __syncthreads();
+    for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) {
+      const double e = P.E[a][i];
+      V.E[P.off[a] + i] = e;
+      nonfinite_e |= !isfinite(e);
+      bad_e |= !(e > 0.0) || !isfinite(e);
+    }
+  // every E must be positive and finite: with E_i <= 0 (an axis on which X
+  // lacks full rank) f falls without bound along that coordinate, so there
+  // is no minimiser; outputs become NaN and the solve stops here
+  {
+    const int any_nonfinite = __syncthreads_or(nonfinite_e);
+    if (__syncthreads_or(bad_e)) {
+      const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+      for (int a = 0; a < P.L; ++a)
+        for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) P.out[a][i] = qnan;
+      if (threadIdx.x == 0) {
+        set_status(status, any_nonfinite ? GMGM_DEV_NONFINITE : GMGM_DEV_INFEASIBLE);
+        st->status = any_nonfinite ? GMGM_E_NONFINITE : GMGM_E_INFEASIBLE;
+        st->newton_iters = 0;
+        st->cg_iters = 0;
+        st->grid_passes = 0;
+        st->n_active = 0;
+        st->fp64_iters = 0;
+        st->rel_kkt = qnan;
+        st->objective = qnan;
+      }
+      return;
+    }
+  }
   // one modality whose traces agree within trace_rtol: scale every axis'
   // spectrum to the mean trace, so the flat shift of the gauge is exact
   if (P.gauge && P.nmod == 1 && P.mk[0] > 1 && P.trace_rtol > 0.0) {

@@ -26,8 +26,15 @@
 // once 8 lanes have one (a lane whose slot is taken inserts at once).  The
 // pair's threshold is the larger of the two lists' minima (each list
 // publishes its minimum in shared memory once full); a stale read only admits
-// more candidates.  Every column left out of a row's two lists has a screened
-// value <= the larger final minimum.  Each row gets 2 kC candidates and two
+// more candidates.
+// Threshold floor (main screen, long sweeps): a sampling pass over every
+// 16th B tile first keeps, per (row, half), the 6 largest 32-column chunk
+// maxima in registers (a branch-free insert per chunk); the 6th of them is a
+// floor below which the full sweep offers nothing.  About 6 x 16 columns of
+// the half lie above it, so a list fills with values that mostly stay: the
+// inserts of a random-order sweep (about kC ln(n / kC) per list) drop to
+// about kC ln 3.  Every column left out of a row's two lists has a screened
+// value <= the larger of the floor and the final minima.  Each row gets 2 kC candidates and two
 // thresholds; the rescore keeps the kC largest screened values and folds the
 // largest dropped one into the row's certification threshold.  All CTAs sweep
 // the B tiles in the same order (L2 reuse).  Every wait is bounded; on
@@ -60,6 +67,21 @@ constexpr int kSlot = 36;                    // stash slot stride (words): 32 va
 constexpr int kBatch = 8;                    // stashed lanes that trigger a drain
 constexpr unsigned kFull = 0xffffffffu;
 constexpr long long kSpin = 1ll << 23;       // polls per bounded wait
+constexpr int kSampK = 6;                    // chunk maxima kept by the sampling pass
+constexpr int kSampMinTiles = 128;           // shortest slice that takes a sampling pass
+
+// Sampling-pass tiles of the slice [t0, t1): every SAMP-th tile, when the
+// slice is long enough for a floor to pay.
+template <int SAMP>
+__host__ __device__ __forceinline__ int sample_tiles(int t0, int t1) {
+  return (SAMP > 0 && t1 - t0 >= kSampMinTiles) ? (t1 - t0 + SAMP - 1) / SAMP : 0;
+}
+
+// B tile of step u of a work item: the ns sampled tiles, then the slice.
+template <int SAMP>
+__device__ __forceinline__ int tile_of(int u, int ns, int t0) {
+  return u < ns ? t0 + u * SAMP : t0 + (u - ns);
+}
 
 // TN columns per B tile; NP products per K step (1: BF16, 3: split);
 // STASH: park hit chunks for batched inserts.
@@ -184,8 +206,8 @@ __device__ __forceinline__ float partner_min(const volatile unsigned long long* 
 __device__ __forceinline__ ListState insert_chunk(const uint32_t (&v)[32], int sj, int self, int n, float* lv, int* li,
                                                   float* smv, int* smp, unsigned long long* pub,
                                                   const volatile unsigned long long* partner, unsigned tag,
-                                                  ListState st) {
-  float thr = fmaxf(st.minv, partner_min(partner, tag));
+                                                  ListState st, float floor_v) {
+  float thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
   uint32_t mask = 0;
 #pragma unroll
   for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(v[e])) > thr ? 1u : 0u) << e;
@@ -196,7 +218,7 @@ __device__ __forceinline__ ListState insert_chunk(const uint32_t (&v)[32], int s
     const int j = sj + e;
     if (x > thr && j < n && j != self) {
       st = offer(lv, li, smv, smp, pub, tag, st, x, j);
-      thr = fmaxf(st.minv, partner_min(partner, tag));
+      thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
     }
   }
   return st;
@@ -205,22 +227,59 @@ __device__ __forceinline__ ListState insert_chunk(const uint32_t (&v)[32], int s
 // A stashed chunk (shared memory) through insert_chunk.
 __device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int self, int n, float* lv, int* li, float* smv,
                                         int* smp, unsigned long long* pub, const volatile unsigned long long* partner,
-                                        unsigned tag, ListState st) {
+                                        unsigned tag, ListState st, float floor_v) {
   uint32_t v[32];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const uint4 w = reinterpret_cast<const uint4*>(slot)[k];
     v[4 * k] = w.x, v[4 * k + 1] = w.y, v[4 * k + 2] = w.z, v[4 * k + 3] = w.w;
   }
-  return insert_chunk(v, sj, self, n, lv, li, smv, smp, pub, partner, tag, st);
+  return insert_chunk(v, sj, self, n, lv, li, smv, smp, pub, partner, tag, st, floor_v);
+}
+
+// max |v| over one 32-value chunk (four short chains).
+__device__ __forceinline__ float chunk_absmax(const uint32_t (&v)[32]) {
+  float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+#pragma unroll
+  for (int e = 0; e < 32; e += 4) {
+    m0 = fmaxf(m0, fabsf(__uint_as_float(v[e + 0])));
+    m1 = fmaxf(m1, fabsf(__uint_as_float(v[e + 1])));
+    m2 = fmaxf(m2, fabsf(__uint_as_float(v[e + 2])));
+    m3 = fmaxf(m3, fabsf(__uint_as_float(v[e + 3])));
+  }
+  return fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+}
+
+// Epilogue warp: wait for accumulator buffer accu & 1, pull this warp's lane
+// quarter of the half's columns in one round trip, and hand the buffer back
+// to the MMA warp.  False (abort raised) when the wait gives up.
+template <class S>
+__device__ __forceinline__ bool take_tile(Bars* bs, uint32_t tmem, int q, int half, long long accu, int lane,
+                                          int* status, uint32_t (&r)[S::kChunks][32]) {
+  const int b = int(accu & 1);
+  if (!__all_sync(kFull, tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin))) {
+    if (lane == 0) raise_abort(bs, status);
+    return false;
+  }
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * S::kTN + half * (S::kTN / 2));
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < S::kChunks; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
+  tc::tmem_ld_wait();
+  tc::fence_before_sync();
+  __syncwarp();
+  if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
+  return true;
 }
 
 // m rows of A (hi, lo planes) against n rows of B (hi, lo planes), the B
 // tiles split into ncs column slices; work item = (row block, slice).  Row p
 // of A is row rows[p] of Psi (p itself when rows is null); slice cs writes
 // its two lists of row p to cand_*[cs * m + p][2 kC] and their minima to
-// thr_out[cs * m + p][2].
-template <int TN, int NP, bool STASH>
+// thr_out[cs * m + p][2].  SAMP > 0: sampling pass over every SAMP-th tile
+// of a long slice first (threshold floor).
+template <int TN, int NP, bool STASH, int SAMP>
 __global__ void __launch_bounds__(kThreads, 1)
     screen_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int m, int n,
@@ -281,7 +340,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::mbar_arrive_expect_tx(&bs->afull, S::kPlanes * kATile);
         tc::tma_load_2d(sA, &tmAh, &bs->afull, 0, rb * kTM);
         if (NP == 3) tc::tma_load_2d(sA + kATile, &tmAl, &bs->afull, 0, rb * kTM);
-        for (int t = t0; t < t1; ++t, ++issued) {
+        const int ns = sample_tiles<SAMP>(t0, t1);
+        for (int u = 0; u < ns + (t1 - t0); ++u, ++issued) {
+          const int t = tile_of<SAMP>(u, ns, t0);
           const int s = int(issued % kStages);
           const uint32_t k = uint32_t(issued / kStages);
           if (!tc::mbar_wait(&bs->empty[s], (k & 1) ^ 1, kSpin)) {
@@ -315,7 +376,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           raise_abort(bs, status);
           break;
         }
-        for (int t = t0; t < t1; ++t, ++used, ++accu) {
+        const int nsteps = sample_tiles<SAMP>(t0, t1) + (t1 - t0);
+        for (int u = 0; u < nsteps; ++u, ++used, ++accu) {
           const int s = int(used % kStages);
           const int b = int(accu & 1);
           if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kStages) & 1, kSpin) ||
@@ -369,38 +431,45 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool parked = false;  // this lane's stash slot holds a chunk
       int sj = 0;           // its first column
       bool ok = true;
-      for (int t = t0; t < t1; ++t, ++accu) {
-        const int b = int(accu & 1);
-        ok = __all_sync(kFull, tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin));
-        if (!ok) {
-          if (lane == 0) raise_abort(bs, status);
-          break;
-        }
-        tc::fence_after_sync();
-        const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * TN + half * (TN / 2));
-        const int j0 = t * TN + half * (TN / 2);
-        // the half's columns in one round trip, then hand the accumulator
-        // back to the MMA warp before scanning
-        uint32_t r[S::kChunks][32];
-        __syncwarp();
+      const int ns = sample_tiles<SAMP>(t0, t1);
+      float floor_v = -1.f;  // no floor until a sampling pass has run
+      if (SAMP > 0 && ns > 0) {
+        float top[kSampK];   // largest chunk maxima so far, descending
 #pragma unroll
-        for (int c = 0; c < S::kChunks; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
-        tc::tmem_ld_wait();
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&bs->acce[b]);
-        const float thr = fmaxf(st.minv, partner_min(partner, tag));
+        for (int x = 0; x < kSampK; ++x) top[x] = -1.f;
+        for (int u = 0; u < ns; ++u, ++accu) {
+          uint32_t r[S::kChunks][32];
+          ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r);
+          if (!ok) break;
+          const int j0 = (t0 + u * SAMP) * TN + half * (TN / 2);
+#pragma unroll
+          for (int c = 0; c < S::kChunks; ++c) {
+            float mx = chunk_absmax(r[c]);
+            const int se = self - (j0 + c * 32);
+            if (se >= 0 && se < 32) {  // the row's own column is no edge
+              mx = 0.f;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) mx = e == se ? mx : fmaxf(mx, fabsf(__uint_as_float(r[c][e])));
+            }
+#pragma unroll
+            for (int x = 0; x < kSampK; ++x) {  // branch-free insert
+              const float hi = fmaxf(top[x], mx);
+              mx = fminf(top[x], mx);
+              top[x] = hi;
+            }
+          }
+        }
+        floor_v = top[kSampK - 1];
+      }
+      for (int t = t0; ok && t < t1; ++t, ++accu) {
+        uint32_t r[S::kChunks][32];
+        ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r);
+        if (!ok) break;
+        const int j0 = t * TN + half * (TN / 2);
+        const float thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
 #pragma unroll
         for (int c = 0; c < S::kChunks; ++c) {
-          float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // four short max chains
-#pragma unroll
-          for (int e = 0; e < 32; e += 4) {
-            m0 = fmaxf(m0, fabsf(__uint_as_float(r[c][e + 0])));
-            m1 = fmaxf(m1, fabsf(__uint_as_float(r[c][e + 1])));
-            m2 = fmaxf(m2, fabsf(__uint_as_float(r[c][e + 2])));
-            m3 = fmaxf(m3, fabsf(__uint_as_float(r[c][e + 3])));
-          }
-          if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr) {
+          if (chunk_absmax(r[c]) > thr) {
             if (STASH && !parked) {
 #pragma unroll
               for (int k = 0; k < 8; ++k)
@@ -408,24 +477,24 @@ __global__ void __launch_bounds__(kThreads, 1)
               parked = true;
               sj = j0 + c * 32;
             } else {
-              st = insert_chunk(r[c], j0 + c * 32, self, n, mlv, mli, msv, msp, mine, partner, tag, st);
+              st = insert_chunk(r[c], j0 + c * 32, self, n, mlv, mli, msv, msp, mine, partner, tag, st, floor_v);
             }
           }
         }
         if (STASH && __popc(__ballot_sync(kFull, parked)) >= kBatch) {
-          if (parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st);
+          if (parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st, floor_v);
           parked = false;
           __syncwarp();
         }
       }
       if (!ok || __any_sync(kFull, aborted(bs))) break;
-      if (STASH && parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st);
+      if (STASH && parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st, floor_v);
       if (p < m) {
         for (int c = 0; c < kC; ++c) {
           cand_idx[out * (2 * kC) + half * kC + c] = c < st.cnt ? mli[c * kLists] : -1;
           cand_val[out * (2 * kC) + half * kC + c] = c < st.cnt ? mlv[c * kLists] : -1.f;
         }
-        thr_out[out * 2 + half] = st.minv;  // -1 while the list was never full
+        thr_out[out * 2 + half] = fmaxf(floor_v, st.minv);  // -1: no floor and the list never full
       }
       __syncwarp();
     }
@@ -509,7 +578,7 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int boxrows) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TN, int NP, bool STASH>
+template <int TN, int NP, bool STASH, int SAMP>
 cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, const void* bh, const void* bl, int n,
                        int ncs, const int* rows, int r, int32_t* cidx, float* cval, float* thr) {
   CUtensorMap mah, mal, mbh, mbl;
@@ -517,7 +586,7 @@ cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, co
   mal = mah;
   mbl = mbh;
   if (NP == 3 && (!make_map(&mal, al, m, kTM) || !make_map(&mbl, bl, n, TN))) return cudaErrorInvalidValue;
-  auto kern = screen_tc_kernel<TN, NP, STASH>;
+  auto kern = screen_tc_kernel<TN, NP, STASH, SAMP>;
   const size_t smem = smem_bytes<Screen<TN, NP, STASH>>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
@@ -528,7 +597,8 @@ cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, co
   return cudaGetLastError();
 }
 
-// main: TN 256, one product, stash; repair: TN 128, split products
+// main: TN 256, one product, stash, sampling pass over every 16th tile;
+// repair: TN 128, split products
 using MainScreen = Screen<256, 1, true>;
 using RepairScreen = Screen<128, 3, false>;
 static_assert(smem_bytes<MainScreen>() <= 232448 && smem_bytes<RepairScreen>() <= 232448, "shared memory");
@@ -561,7 +631,7 @@ cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, in
     prep_tc_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, A, B);
   }
   note_launch(2);
-  return run_screen<256, 1, true>(h, A, nullptr, int(d), B, nullptr, int(d), 1, nullptr, r, cidx, cval, thr);
+  return run_screen<256, 1, true, 16>(h, A, nullptr, int(d), B, nullptr, int(d), 1, nullptr, r, cidx, cval, thr);
 }
 
 cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,
@@ -580,7 +650,7 @@ cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void
     prep_split_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, rows, m, Bh, Bl, Ah, Al);
   }
   note_launch(2);
-  return run_screen<128, 3, false>(h, Ah, Al, m, Bh, Bl, int(d), ncs, rows, r, cidx, cval, thr);
+  return run_screen<128, 3, false, 0>(h, Ah, Al, m, Bh, Bl, int(d), ncs, rows, r, cidx, cval, thr);
 }
 
 }  // namespace gmgm

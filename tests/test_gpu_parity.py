@@ -248,12 +248,35 @@ def test_eigsolve_warm_start_and_fp64_only(g, cuda_dev):
         torch.testing.assert_close(a, b, rtol=1e-8, atol=0)
 
 
+@pytest.mark.parametrize("bad,code", [(0.0, -6), (-1.0, -6), (float("nan"), -4), (float("inf"), -4)])
+def test_eigsolve_rejects_nonpositive_or_nonfinite_E(g, cuda_dev, bad, code):
+    # a zero eigenvalue (X without full rank on an axis) leaves f unbounded
+    # below: no iteration runs, the outputs are NaN, the status says why
+    x, _, _ = planted_c1()
+    e_r, _, e_c, _ = osp.two_axis_spectra(x, 20, 100)
+    e_c = e_c.copy()
+    e_c[-1] = bad
+    E = [torch.from_numpy(e).to(cuda_dev) for e in (e_r, e_c)]
+    with pytest.raises(g.GmgmError) as ei:
+        g.eigsolve(E, [(0, 1)])
+    assert ei.value.code == code
+    h = g.handle(cuda_dev)
+    bits = h.device_status()
+    assert bits & (0x4 if code == -6 else 0x1)
+    # the handle stays usable: the same call on valid spectra converges
+    e_c[-1] = e_c[-2] * 0.5
+    E = [torch.from_numpy(e).to(cuda_dev) for e in (e_r, e_c)]
+    lams, st = g.eigsolve(E, [(0, 1)])
+    assert st["status"] == 0 and all(torch.isfinite(l).all() for l in lams)
+
+
 # ---- top-k ------------------------------------------------------------------------
 
-def _check_topk(V64, lam, k, idx, val):
-    """Stage-wise parity: the oracle's FP64 top-k of the same V, psi."""
-    ref_i, ref_v = orc.topk_rows(V64, lam, k)
-    gap = orc.topk_gap(V64, lam, k)
+def _check_topk(V64, lam, k, idx, val, rows=None):
+    """Stage-wise parity: the oracle's FP64 top-k of the same V, psi (of the
+    given rows only, when ``rows`` is set; idx/val are then those rows')."""
+    ref_i, ref_v = orc.topk_rows(V64, lam, k, rows=rows)
+    gap = orc.topk_gap(V64, lam, k, rows=rows)
     ok = gap > 1e-5
     assert np.array_equal(np.sort(idx[ok], 1), np.sort(ref_i[ok], 1))
     # order inside the list follows the exact values
@@ -292,6 +315,36 @@ def test_topk_bf16_tensor_core_screen(g, cuda_dev, d, r, k):
     assert st["screen_err_ratio"] <= 1.0, st
     if d > 64 and k <= 20:  # with k near the 32 candidate slots no row can be certified
         assert st["rows_uncertified"] <= 0.5 * d, st
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_topk_bf16_long_sweep_sampled_rows(g, cuda_dev, clustered):
+    # 40,000 columns: 157 B tiles per row block, long enough for the main
+    # screen's sampling pass (threshold floor from every 16th tile); the
+    # oracle's FP64 top-k of 500 sampled rows, and a valid list on every row.
+    # Clustered rows (200 centroids + noise) put a row's strongest partners
+    # in few columns, the case where a floor is most often too high for a
+    # half's list to fill
+    rng = _rng(41 + clustered)
+    d, r, k = 40000, 50, 10
+    if clustered:
+        cent = rng.standard_normal((200, r))
+        V = cent[rng.integers(0, 200, d)] + 0.3 * rng.standard_normal((d, r))
+    else:
+        V = rng.standard_normal((d, r))
+    V = V.astype(np.float32)
+    lam = rng.uniform(0.1, 2.0, r)
+    idx, val, st = g.topk_network(torch.from_numpy(V).to(cuda_dev), torch.from_numpy(lam).to(cuda_dev), k,
+                                  prec=g.BF16)
+    idx, val = idx.cpu().numpy(), val.cpu().numpy()
+    assert st["screen_err_ratio"] <= 1.0, st
+    srt = np.sort(idx, 1)
+    assert np.all(srt[:, 1:] != srt[:, :-1]) and np.all(idx >= 0) and np.all(idx < d)
+    assert not np.any(idx == np.arange(d)[:, None])
+    rows = np.sort(rng.choice(d, 500, replace=False))
+    frac = _check_topk(V.astype(np.float64), lam, k, idx[rows], val[rows], rows=rows)
+    assert frac > 0.9
+    assert st["rows_exact"] <= d // 100, st
 
 
 def test_topk_fp64_input_and_ties(g, cuda_dev):
