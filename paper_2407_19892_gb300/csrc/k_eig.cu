@@ -16,41 +16,71 @@
 #include <cfloat>
 
 #include "device.cuh"
+#include "df.cuh"
 #include "internal.cuh"
 
 namespace gmgm {
 namespace {
 
-constexpr int kTriThreads = 256;
+constexpr int kTriThreads = 512;
 constexpr int kBatch = 8;     // independent row loads per lane in flight
 constexpr int kInvIters = 2;  // inverse-iteration solves (bisection eigenvalues are accurate to ~eps)
 
-__global__ void copy_sym_kernel(const double* __restrict__ S, int64_t lds, int n, double* __restrict__ A) {
+// max |S_ij| over the lower triangle, as the bits of a non-negative double
+// (ordered like the values), into *amax (zeroed before).
+__global__ void absmax_kernel(const double* __restrict__ S, int64_t lds, int n, unsigned long long* amax) {
+  unsigned long long m = 0;
+  const int64_t total = int64_t(n) * n;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    if (j <= i) m = max(m, static_cast<unsigned long long>(__double_as_longlong(fabs(S[i * lds + j]))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
+}
+
+// Exponent e with max |S| = f 2^e, f in [0.5, 1): the matrix is reduced as
+// 2^-e S (exact), so the double-float entries stay far from the FP32
+// overflow and underflow thresholds; 0 for a zero or non-finite maximum.
+__device__ __forceinline__ int scale_exp(const unsigned long long* amax) {
+  const double smax = __longlong_as_double(static_cast<long long>(*amax));
+  if (!(smax > 0.0) || !isfinite(smax)) return 0;
+  int e;
+  frexp(smax, &e);
+  return e;
+}
+
+__global__ void copy_sym_kernel(const double* __restrict__ S, int64_t lds, int n,
+                                const unsigned long long* __restrict__ amax, dfl* __restrict__ A) {
   const int64_t i = int64_t(blockIdx.y) * blockDim.y + threadIdx.y;
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n || j >= n) return;
+  const double sc = ldexp(1.0, -scale_exp(amax));
   // lower triangle is authoritative
-  A[i * n + j] = i >= j ? S[i * lds + j] : S[j * lds + i];
+  A[i * n + j] = df_from((i >= j ? S[i * lds + j] : S[j * lds + i]) * sc);
 }
 
 // Householder of x (length m, in smem): v (v[0] = 1) and tau with
-// (I - tau v v^T) x = beta e_0.  Every CTA runs it on identical data.
-__device__ __forceinline__ void householder(double* x, int m, double* red, double& tau, double& beta) {
-  double ss = 0.0;
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) ss += x[i] * x[i];
-  const double tail = block_sum(ss, red);
-  const double x0 = x[0];
-  tau = 0.0;
+// (I - tau v v^T) x = beta e_0.  Every CTA runs it on identical data, all
+// in double-float: every warp evaluates the scalars, and on this part a
+// warp's FP64 instruction costs dozens of FP32 ones.
+__device__ __forceinline__ void householder(dfl* x, int m, dfl* red, dfl& tau, dfl& beta) {
+  dfl ss = df_zero();
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) ss = df_fma(ss, x[i], x[i]);
+  const dfl tail = df_block_sum(ss, red);
+  const dfl x0 = x[0];
+  tau = df_zero();
   beta = x0;
-  if (tail > 0.0) {
-    const double nrm = sqrt(x0 * x0 + tail);
-    beta = x0 >= 0.0 ? -nrm : nrm;
-    tau = (beta - x0) / beta;
-    const double sc = 1.0 / (x0 - beta);
-    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= sc;
+  if (tail.h > 0.f) {
+    const dfl nrm = df_sqrt(df_fma(tail, x0, x0));
+    beta = x0.h >= 0.f ? df_neg(nrm) : nrm;
+    tau = df_div(df_add(beta, df_neg(x0)), beta);
+    const dfl sc = df_div(dfl{1.f, 0.f}, df_add(x0, df_neg(beta)));
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = df_mul(x[i], sc);
   }
   __syncthreads();
-  if (threadIdx.x == 0) x[0] = 1.0;
+  if (threadIdx.x == 0) x[0] = dfl{1.f, 0.f};
   __syncthreads();
 }
 
@@ -61,68 +91,90 @@ __device__ __forceinline__ void householder(double* x, int m, double* red, doubl
 //   v = reflector k (rows/cols k+1..n-1), u = reflector k+1 (k+2..n-1),
 //   P = tau_{k+1} A_{k+1} u (written by row owners, read after the barrier;
 //   double-buffered so a CTA still reading step k's P never sees step k+1's).
-__global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, double* dv, double* ev, double* Vh,
-                                                              double* tau_out, double* P, unsigned* bar,
-                                                              int* status) {
-  extern __shared__ double sm[];
-  double* v = sm;          // [n]
-  double* w = sm + n;      // [n]
-  double* u = sm + 2 * n;  // [n]
-  __shared__ double red[33];
+// The matrix, the reflectors and P are double-float (FP32 pipe); the
+// reflectors' scalars are FP64.  Outputs: T's diagonal dv and off-diagonal
+// ev (scaled back by 2^e, exact), tau, and the reflectors in Vh (FP64, the
+// exact values of the double-float vectors the reduction applied).
+__global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, const unsigned long long* amax,
+                                                              double* dv, double* ev, double* Vh, double* tau_out,
+                                                              dfl* P, unsigned* bar, int* status) {
+  extern __shared__ dfl tri_sm[];
+  dfl* v = tri_sm;          // [n]
+  dfl* w = tri_sm + n;      // [n]
+  dfl* u = tri_sm + 2 * n;  // [n]
+  __shared__ dfl red[33];
   const unsigned nb = gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int gwarp = blockIdx.x * nwarps + warp, total_warps = nb * nwarps;
+  const int gthread = blockIdx.x * blockDim.x + threadIdx.x, total_threads = nb * blockDim.x;
+  const double unscale = ldexp(1.0, scale_exp(amax));
   // prologue: reflector 0 from row 0, P = tau_0 A[1:,1:] v
-  double tk, beta;
+  dfl tk, beta;
   {
     const int m = n - 1;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = __ldcg(A + 1 + i);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const float2 a = __ldcg(reinterpret_cast<const float2*>(A) + 1 + i);
+      v[i] = dfl{a.x, a.y};
+    }
     __syncthreads();
     householder(v, m, red, tk, beta);
-    if (blockIdx.x == 0) {
-      if (threadIdx.x == 0) {
-        dv[0] = __ldcg(A);
-        ev[0] = beta;
-        tau_out[0] = tk;
-      }
-      for (int i = threadIdx.x; i < m; i += blockDim.x) Vh[1 + i] = v[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const float2 a00 = __ldcg(reinterpret_cast<const float2*>(A));
+      dv[0] = df_val(dfl{a00.x, a00.y}) * unscale;
+      ev[0] = df_val(beta) * unscale;
+      tau_out[0] = df_val(tk);
     }
+    for (int i = gthread; i < m; i += total_threads) Vh[1 + i] = df_val(v[i]);
+    const dfl td = tk;
     for (int i = gwarp; i < m; i += total_warps) {
-      const double* row = A + int64_t(1 + i) * n + 1;
-      double s = 0.0;
-      for (int j0 = lane; j0 < m; j0 += 32 * kBatch) {
-        double a[kBatch];
+      const float2* row = reinterpret_cast<const float2*>(A) + int64_t(1 + i) * n + 1;
+      dfl acc[kBatch];
 #pragma unroll
-        for (int q = 0; q < kBatch; ++q) a[q] = j0 + 32 * q < m ? __ldcg(row + j0 + 32 * q) : 0.0;
+      for (int q = 0; q < kBatch; ++q) acc[q] = df_zero();
+      for (int j0 = lane; j0 < m; j0 += 32 * kBatch) {
+        float2 a[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) a[q] = j0 + 32 * q < m ? __ldcg(row + j0 + 32 * q) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < kBatch; ++q)
-          if (j0 + 32 * q < m) s += a[q] * v[j0 + 32 * q];
+          if (j0 + 32 * q < m) acc[q] = df_fma(acc[q], dfl{a[q].x, a[q].y}, v[j0 + 32 * q]);
       }
-      s = warp_sum(s);
-      if (lane == 0) P[i] = tk * s;
+#pragma unroll
+      for (int q = 1; q < kBatch; ++q) acc[0] = df_add(acc[0], acc[q]);
+      const dfl s = df_warp_sum(acc[0]);
+      if (lane == 0) P[i] = df_mul(td, s);
     }
     if (!grid_barrier(bar, nb, status)) return;
   }
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;  // size of the trailing block of step k
     // w = P - K v, K = tau_k (P.v) / 2
-    double pv = 0.0;
-    const double* Pc = P + (k & 1) * int64_t(n);
-    double* Pn = P + ((k + 1) & 1) * int64_t(n);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) pv += __ldcg(Pc + i) * v[i];
-    pv = block_sum(pv, red);
-    const double K = 0.5 * tk * pv;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = tk != 0.0 ? __ldcg(Pc + i) - K * v[i] : 0.0;
+    const dfl* Pc = P + (k & 1) * int64_t(n);
+    dfl* Pn = P + ((k + 1) & 1) * int64_t(n);
+    dfl pv = df_zero();
+#pragma unroll 4
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const float2 pc = __ldcg(reinterpret_cast<const float2*>(Pc) + i);
+      w[i] = dfl{pc.x, pc.y};
+      pv = df_fma(pv, w[i], v[i]);
+    }
+    const bool live = tk.h != 0.f;  // reflector k is not the identity
+    const dfl nK = df_mul(dfl{-0.5f * tk.h, -0.5f * tk.l}, df_block_sum(pv, red));  // -tau_k (P.v) / 2
+    for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = live ? df_fma(w[i], nK, v[i]) : df_zero();
     __syncthreads();
     // row k+1 of the updated matrix, columns k+1..n-1 -> u[0..m-1]
     {
-      const double* row = A + int64_t(k + 1) * n + k + 1;
-      const double v0 = v[0], w0 = w[0];
-      for (int j = threadIdx.x; j < m; j += blockDim.x) u[j] = __ldcg(row + j) - (v0 * w[j] + w0 * v[j]);
+      const float2* row = reinterpret_cast<const float2*>(A) + int64_t(k + 1) * n + k + 1;
+      const dfl v0 = v[0], w0 = w[0];
+#pragma unroll 4
+      for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const float2 a = __ldcg(row + j);
+        u[j] = df_sub2(dfl{a.x, a.y}, v0, w[j], w0, v[j]);
+      }
     }
     __syncthreads();
-    const double dnext = u[0];
-    double tn = 0.0, bn = 0.0;
+    const dfl dnext = u[0];
+    dfl tn = df_zero(), bn;
     const bool more = k + 3 < n;  // a reflector k+1 exists
     if (more) {
       householder(u + 1, m - 1, red, tn, bn);  // u+1 holds x = row entries k+2..n-1
@@ -130,41 +182,54 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, 
       bn = u[1];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      dv[k + 1] = dnext;
-      ev[k + 1] = bn;
-      if (more) tau_out[k + 1] = tn;
+      dv[k + 1] = df_val(dnext) * unscale;
+      ev[k + 1] = df_val(bn) * unscale;
+      if (more) tau_out[k + 1] = df_val(tn);
     }
-    if (more && blockIdx.x == 0)
-      for (int i = threadIdx.x; i < m - 1; i += blockDim.x) Vh[int64_t(k + 1) * n + k + 2 + i] = u[1 + i];
+    if (more)
+      for (int i = gthread; i < m - 1; i += total_threads) Vh[int64_t(k + 1) * n + k + 2 + i] = df_val(u[1 + i]);
     // fused pass: rows i, cols j in k+2..n-1 (local index t = i - (k+1) >= 1)
+    const bool upd = live;
+    const dfl tnd = tn;
     for (int it = gwarp; it < (m - 1); it += total_warps) {
       const int t = 1 + it;
-      double* row = A + int64_t(k + 1 + t) * n + k + 2;
-      const double vi = v[t], wi = w[t];
-      double s = 0.0;
+      float2* row = reinterpret_cast<float2*>(A) + int64_t(k + 1 + t) * n + k + 2;
+      const dfl vi = v[t], wi = w[t];
       const int mm = m - 1;
-      // kBatch independent L2 loads in flight per lane before any store
+      dfl acc[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) acc[q] = df_zero();
+      // kBatch independent L2 loads per lane; the next batch's are issued
+      // before this batch's update, so two batches are in flight
+      float2 a[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) a[q] = lane + 32 * q < mm ? __ldcg(row + lane + 32 * q) : make_float2(0.f, 0.f);
       for (int j0 = lane; j0 < mm; j0 += 32 * kBatch) {
-        double a[kBatch];
+        float2 nx[kBatch];
 #pragma unroll
         for (int q = 0; q < kBatch; ++q) {
-          const int jj = j0 + 32 * q;
-          a[q] = jj < mm ? __ldcg(row + jj) : 0.0;
+          const int jj = j0 + 32 * (kBatch + q);
+          nx[q] = jj < mm ? __ldcg(row + jj) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < kBatch; ++q) {
           const int jj = j0 + 32 * q;
           if (jj < mm) {
-            if (tk != 0.0) {
-              a[q] -= vi * w[1 + jj] + wi * v[1 + jj];
-              row[jj] = a[q];
+            dfl x{a[q].x, a[q].y};
+            if (upd) {
+              x = df_sub2(x, vi, w[1 + jj], wi, v[1 + jj]);
+              row[jj] = make_float2(x.h, x.l);
             }
-            s += a[q] * u[1 + jj];
+            acc[q] = df_fma(acc[q], x, u[1 + jj]);
           }
         }
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) a[q] = nx[q];
       }
-      s = warp_sum(s);
-      if (lane == 0 && more) Pn[it] = tn * s;
+#pragma unroll
+      for (int q = 1; q < kBatch; ++q) acc[0] = df_add(acc[0], acc[q]);
+      const dfl s = df_warp_sum(acc[0]);
+      if (lane == 0 && more) Pn[it] = df_mul(tnd, s);
     }
     // next step's reflector (after every warp of the CTA is done reading v, w)
     __syncthreads();
@@ -172,14 +237,18 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(double* A, int n, 
     tk = tn;
     if (!grid_barrier(bar, nb, status)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) dv[n - 1] = __ldcg(A + int64_t(n - 1) * n + n - 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const float2 a = __ldcg(reinterpret_cast<const float2*>(A) + int64_t(n - 1) * n + n - 1);
+    dv[n - 1] = df_val(dfl{a.x, a.y}) * unscale;
+  }
 }
 
-__global__ void tiny_tridiag_kernel(const double* A, int n, double* dv, double* ev) {
-  dv[0] = A[0];
+// n = 1 or 2: S is already tridiagonal (lower triangle authoritative).
+__global__ void tiny_tridiag_kernel(const double* S, int64_t lds, int n, double* dv, double* ev) {
+  dv[0] = S[0];
   if (n == 2) {
-    dv[1] = A[3];
-    ev[0] = A[1];
+    dv[1] = S[lds + 1];
+    ev[0] = S[lds];
   }
 }
 
@@ -582,7 +651,9 @@ __global__ void output_kernel(const double* __restrict__ Zc, int n, int cnt, dou
 constexpr int kInvBatch = 4096;
 
 struct EigScratch {
-  double *A, *Vh, *tau, *dv, *ev, *e2, *P, *info, *lam, *lamv, *u0, *u1, *u2, *Z, *Zc, *Uwy, *Ywy;
+  dfl *A, *P;  // the matrix being reduced and the mat-vec, double-float
+  double *Vh, *tau, *dv, *ev, *e2, *info, *lam, *lamv, *u0, *u1, *u2, *Z, *Zc, *Uwy, *Ywy;
+  unsigned long long* amax;
   size_t bytes;
 };
 
@@ -592,13 +663,14 @@ EigScratch carve_eig(void* base, int64_t d, int32_t nval, int32_t nvec) {
   Carve c(base);
   EigScratch s;
   const int64_t B = std::max<int64_t>(1, std::min<int64_t>(nvec, kInvBatch));
-  s.A = c.take<double>(d * d);
+  s.A = c.take<dfl>(d * d);
   s.Vh = c.take<double>(d * d);
   s.tau = c.take<double>(d);
   s.dv = c.take<double>(d);
   s.ev = c.take<double>(d);
   s.e2 = c.take<double>(d);
-  s.P = c.take<double>(2 * d);
+  s.P = c.take<dfl>(2 * d);
+  s.amax = c.take<unsigned long long>(1);
   s.info = c.take<double>(8);
   s.lam = c.take<double>(std::max(nval, 1));
   s.lamv = c.take<double>(std::max(nvec, 1));
@@ -624,16 +696,20 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
   EigScratch s = carve_eig(scratch, d64, nval, nvec);
   cudaError_t e;
   int launches = 0;
-  {
+  if (n >= 3) {
+    if ((e = cudaMemsetAsync(s.amax, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    const int64_t total = int64_t(n) * n;
+    absmax_kernel<<<unsigned(std::min<int64_t>((total + 255) / 256, int64_t(h->num_sms) * 8)), 256, 0, st>>>(
+        S, lds, n, s.amax);
     dim3 b(32, 8), g(unsigned((n + 31) / 32), unsigned((n + 7) / 8));
-    copy_sym_kernel<<<g, b, 0, st>>>(S, lds, n, s.A);
-    ++launches;
+    copy_sym_kernel<<<g, b, 0, st>>>(S, lds, n, s.amax, s.A);
+    launches += 2;
   }
   if ((e = cudaMemsetAsync(s.Vh, 0, size_t(n) * n * sizeof(double), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(s.tau, 0, size_t(n) * sizeof(double), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(s.ev, 0, size_t(n) * sizeof(double), st)) != cudaSuccess) return e;
   if (n >= 3) {
-    const size_t smem = size_t(3) * n * sizeof(double);
+    const size_t smem = size_t(3) * n * sizeof(dfl);
     if ((e = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) !=
         cudaSuccess)
       return e;
@@ -647,18 +723,20 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
     const unsigned want = unsigned((int64_t(n) * n + 16383) / 16384);
     blocks = std::min(blocks, std::max(1u, want));
     if ((e = cudaMemsetAsync(h->d_barrier, 0, 64, st)) != cudaSuccess) return e;
-    double* A = s.A;
-    double *dv = s.dv, *ev = s.ev, *Vh = s.Vh, *tau = s.tau, *P = s.P;
+    dfl* A = s.A;
+    dfl* P = s.P;
+    const unsigned long long* amax = s.amax;
+    double *dv = s.dv, *ev = s.ev, *Vh = s.Vh, *tau = s.tau;
     unsigned* bar = h->d_barrier;
     int* status = h->d_status;
     int nn = n;
-    void* args[] = {&A, &nn, &dv, &ev, &Vh, &tau, &P, &bar, &status};
+    void* args[] = {&A, &nn, &amax, &dv, &ev, &Vh, &tau, &P, &bar, &status};
     if ((e = cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(kTriThreads), args, smem,
                                          st)) != cudaSuccess)
       return e;
   } else {
     // n = 1 or 2: already tridiagonal
-    tiny_tridiag_kernel<<<1, 1, 0, st>>>(s.A, n, s.dv, s.ev);
+    tiny_tridiag_kernel<<<1, 1, 0, st>>>(S, lds, n, s.dv, s.ev);
   }
   tri_info_kernel<<<1, 256, 0, st>>>(s.dv, s.ev, n, s.e2, s.info);
   launches += 2;

@@ -56,7 +56,8 @@ namespace {
 
 constexpr int kTM = 128;                     // rows per row block (MMA M)
 constexpr int kKP = 64;                      // padded K (bf16 elements, one 128-byte row)
-constexpr int kStages = 3;
+constexpr int kMaxStages = 4;                // B-tile ring depth at most
+constexpr size_t kSmemCap = 232448;          // dynamic shared memory per CTA
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kATile = kTM * kKP * 2;        // 16 KB per plane
@@ -83,22 +84,9 @@ __device__ __forceinline__ int tile_of(int u, int ns, int t0) {
   return u < ns ? t0 + u * SAMP : t0 + (u - ns);
 }
 
-// TN columns per B tile; NP products per K step (1: BF16, 3: split);
-// STASH: park hit chunks for batched inserts.
-template <int TN, int NP, bool STASH>
-struct Screen {
-  static constexpr int kTN = TN;
-  static constexpr int kChunks = TN / 64;                 // 32-column chunks per half
-  static constexpr int kPlanes = NP == 3 ? 2 : 1;         // hi (+ lo)
-  static constexpr int kBTile = TN * kKP * 2;             // per plane
-  static constexpr int kTmemCols = 2 * TN;
-  static constexpr size_t kLists_ = size_t(2) * kC * kLists * 4 + size_t(2) * kNSub * kLists * 4 + size_t(kLists) * 8;
-  static constexpr size_t kStash = STASH ? size_t(32) * kEpiWarps * kSlot * 4 : 0;
-};
-
 struct __align__(8) Bars {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
   uint64_t accf[2];
   uint64_t acce[2];
   uint64_t afull;
@@ -108,10 +96,28 @@ struct __align__(8) Bars {
   int abort;
 };
 
+// TN columns per B tile; NP products per K step (1: BF16, 3: split);
+// STASH: park hit chunks for batched inserts.  The B ring takes as many
+// stages (up to kMaxStages) as the shared memory left over holds.
+template <int TN, int NP, bool STASH>
+struct Screen {
+  static constexpr int kTN = TN;
+  static constexpr int kChunks = TN / 64;                 // 32-column chunks per half
+  static constexpr int kPlanes = NP == 3 ? 2 : 1;         // hi (+ lo)
+  static constexpr int kBTile = TN * kKP * 2;             // per plane
+  static constexpr int kTmemCols = 2 * TN;
+  static constexpr size_t kLists_ = size_t(2) * kC * kLists * 4 + size_t(2) * kNSub * kLists * 4 + size_t(kLists) * 8;
+  static constexpr size_t kStash = STASH ? size_t(32) * kEpiWarps * kSlot * 4 : 0;
+  static constexpr size_t kFixed = 1024 /*align slack*/ + size_t(kPlanes) * kATile + kLists_ + kStash + sizeof(Bars);
+  static constexpr int kStages = int((kSmemCap - kFixed) / (size_t(kPlanes) * kBTile)) < kMaxStages
+                                     ? int((kSmemCap - kFixed) / (size_t(kPlanes) * kBTile))
+                                     : kMaxStages;
+  static_assert(kStages >= 2, "B-tile ring");
+};
+
 template <class S>
 constexpr size_t smem_bytes() {
-  return 1024 /*align slack*/ + size_t(S::kPlanes) * kATile + size_t(kStages) * S::kPlanes * S::kBTile + S::kLists_ +
-         S::kStash + sizeof(Bars);
+  return S::kFixed + size_t(S::kStages) * S::kPlanes * S::kBTile;
 }
 
 __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;                                  // [kPlanes][kATile]
   uint8_t* sB = sA + S::kPlanes * kATile;              // [kStages][kPlanes][kBTile]
-  float* lv = reinterpret_cast<float*>(sB + kStages * S::kPlanes * S::kBTile);
+  float* lv = reinterpret_cast<float*>(sB + S::kStages * S::kPlanes * S::kBTile);
   int* li = reinterpret_cast<int*>(lv + kC * kLists);
   float* smv_all = reinterpret_cast<float*>(li + kC * kLists);        // [kNSub][kLists] sub-list minima
   int* smp_all = reinterpret_cast<int*>(smv_all + kNSub * kLists);     // [kNSub][kLists] their slots
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   Bars* bs = reinterpret_cast<Bars*>(reinterpret_cast<uint8_t*>(stash) + S::kStash);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
+    for (int s = 0; s < S::kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
     for (int b = 0; b < 2; ++b) tc::mbar_init(&bs->accf[b], 1), tc::mbar_init(&bs->acce[b], kEpiWarps);
     tc::mbar_init(&bs->afull, 1);
     tc::mbar_init(&bs->aempty, 1);
@@ -343,8 +349,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ns = sample_tiles<SAMP>(t0, t1);
         for (int u = 0; u < ns + (t1 - t0); ++u, ++issued) {
           const int t = tile_of<SAMP>(u, ns, t0);
-          const int s = int(issued % kStages);
-          const uint32_t k = uint32_t(issued / kStages);
+          const int s = int(issued % S::kStages);
+          const uint32_t k = uint32_t(issued / S::kStages);
           if (!tc::mbar_wait(&bs->empty[s], (k & 1) ^ 1, kSpin)) {
             raise_abort(bs, status);
             break;
@@ -358,8 +364,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (aborted(bs)) {
         // let the loads already in flight land before the CTA can exit
-        for (long long x = issued > kStages ? issued - kStages : 0; x < issued; ++x)
-          tc::mbar_wait(&bs->full[x % kStages], uint32_t(x / kStages) & 1, kSpin);
+        for (long long x = issued > S::kStages ? issued - S::kStages : 0; x < issued; ++x)
+          tc::mbar_wait(&bs->full[x % S::kStages], uint32_t(x / S::kStages) & 1, kSpin);
       }
     }
   } else if (warp == 1) {
@@ -378,9 +384,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const int nsteps = sample_tiles<SAMP>(t0, t1) + (t1 - t0);
         for (int u = 0; u < nsteps; ++u, ++used, ++accu) {
-          const int s = int(used % kStages);
+          const int s = int(used % S::kStages);
           const int b = int(accu & 1);
-          if (!tc::mbar_wait(&bs->full[s], uint32_t(used / kStages) & 1, kSpin) ||
+          if (!tc::mbar_wait(&bs->full[s], uint32_t(used / S::kStages) & 1, kSpin) ||
               !tc::mbar_wait(&bs->acce[b], (uint32_t(accu >> 1) & 1) ^ 1, kSpin)) {
             raise_abort(bs, status);
             break;
@@ -601,7 +607,7 @@ cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, co
 // repair: TN 128, split products
 using MainScreen = Screen<256, 1, true>;
 using RepairScreen = Screen<128, 3, false>;
-static_assert(smem_bytes<MainScreen>() <= 232448 && smem_bytes<RepairScreen>() <= 232448, "shared memory");
+static_assert(smem_bytes<MainScreen>() <= kSmemCap && smem_bytes<RepairScreen>() <= kSmemCap, "shared memory");
 
 }  // namespace
 
