@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "device.cuh"
+#include "df.cuh"
 #include "internal.cuh"
 #include "topk_common.cuh"
 
@@ -170,6 +171,22 @@ __device__ __forceinline__ double vload(const void* V, int v64, int64_t idx) {
 
 __device__ __forceinline__ bool better(double a, int ja, double b, int jb) { return a > b || (a == b && ja < jb); }
 
+// (|value|, column) order on double-float magnitudes: larger first, then
+// the lower column.
+__device__ __forceinline__ bool df_better(dfl a, int ja, dfl b, int jb) {
+  return a.h > b.h || (a.h == b.h && (a.l > b.l || (a.l == b.l && ja < jb)));
+}
+
+__device__ __forceinline__ dfl df_shfl(dfl a, int src) {
+  return dfl{__shfl_sync(0xffffffffu, a.h, src), __shfl_sync(0xffffffffu, a.l, src)};
+}
+
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // (screened value, column) order of the candidate merge; empty slots are
 // (-1, INT_MAX) and sort last.
 __device__ __forceinline__ bool fbetter(float a, int ja, float b, int jb) { return a > b || (a == b && ja < jb); }
@@ -218,6 +235,14 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
                                const unsigned* __restrict__ colmax_bits, double u, int32_t* __restrict__ idx_out,
                                float* __restrict__ val_out, int* __restrict__ flag_list, int* __restrict__ flag_count,
                                unsigned* __restrict__ err_bits) {
+  extern __shared__ dfl rs_psi[];  // [r] psi as double-float, then [r] |psi| rounded up (FP32)
+  float* psi_up = reinterpret_cast<float*>(rs_psi + r);
+  for (int q = threadIdx.x; q < r; q += blockDim.x) {
+    rs_psi[q] = df_from(psi[q]);
+    psi_up[q] = __double2float_ru(fabs(psi[q]));
+  }
+  __syncthreads();
+  const float u_up = __double2float_ru(u);
   const int lane = threadIdx.x & 31;
   const int64_t m = count_dev ? int64_t(*count_dev) : m_host;
   const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -226,20 +251,20 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
     const int64_t i = rows ? int64_t(rows[mi]) : mi;
     int j;
     float cv;
-    double t;
+    float t;  // every input is an FP32 screened value: the maximum is exact in FP32
     if (nl == 1) {
       j = cidx[mi * kC + lane];
       cv = cval[mi * kC + lane];
-      t = double(thr[mi]);
+      t = thr[mi];
     } else {
-      t = -1.0;
+      t = -1.f;
       for (int l = 0; l < nl; ++l) {
         const int64_t pair = int64_t(l >> 1) * lstride + mi;
         const int64_t base = pair * (2 * kC) + (l & 1) * kC;
         int j2 = cidx[base + lane];
         float v2 = cval[base + lane];
         if (j2 < 0) v2 = -1.f, j2 = INT_MAX;
-        t = fmax(t, double(thr[pair * 2 + (l & 1)]));
+        t = fmaxf(t, thr[pair * 2 + (l & 1)]);
         if (l == 0) {
           cv = v2, j = j2;
           warp_sort_pairs(cv, j, true);
@@ -249,54 +274,83 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
         const bool keep2 = fbetter(v2, j2, cv, j);
         const float dropped = keep2 ? cv : v2;
         if (keep2) cv = v2, j = j2;
-        t = fmax(t, double(warp_max(dropped)));
+        t = fmaxf(t, warp_max_f(dropped));
         if (l + 1 < nl) warp_merge_desc(cv, j);
       }
       if (j == INT_MAX) j = -1;
     }
-    double ex = 0.0;
-    if (j >= 0) {
-      for (int q = 0; q < r; ++q) ex += vload(V, v64, i * ldv + q) * psi[q] * vload(V, v64, int64_t(j) * ldv + q);
+    // exact value of the lane's candidate: an FP64 V in FP64; an FP32 V in
+    // double-float (a_q = V_iq psi_q exact to 2^-48 from lane q % 32, the
+    // products with V_jq and the sum by TwoProd/TwoSum).  Its error, about
+    // 2^-46 of sum_q |a_q V_jq|, is far inside the slack of the screen bound.
+    dfl ex = df_zero();
+    if (v64) {
+      double e = 0.0;
+      const double* Vd = static_cast<const double*>(V);
+      if (j >= 0)
+        for (int q = 0; q < r; ++q) e += Vd[i * ldv + q] * psi[q] * Vd[int64_t(j) * ldv + q];
+      ex = df_from(e);
+    } else {
+      const float* Vf = static_cast<const float*>(V);
+      const float* vj = Vf + int64_t(j >= 0 ? j : 0) * ldv;
+      for (int q0 = 0; q0 < r; q0 += 32) {
+        const int qn = min(32, r - q0);
+        const dfl aq = lane < qn ? df_mul(dfl{Vf[i * ldv + q0 + lane], 0.f}, rs_psi[q0 + lane]) : df_zero();
+#pragma unroll 8
+        for (int c = 0; c < qn; ++c) {
+          const dfl a = df_shfl(aq, c);
+          if (j >= 0) ex = df_fma(ex, a, dfl{vj[q0 + c], 0.f});
+        }
+      }
     }
     // self-check of the screen: |screened - |exact|| must stay within the bound
-    const double serr = j >= 0 ? fabs(double(cv) - fabs(ex)) : 0.0;
-    double key = j >= 0 ? fabs(ex) : -1.0;
+    const dfl aex = ex.h < 0.f ? df_neg(ex) : ex;
+    const float serr = j >= 0 ? fabsf(__fsub_rn(cv, aex.h)) : 0.f;
+    dfl key = j >= 0 ? aex : dfl{-1.f, 0.f};
     int kj = j >= 0 ? j : INT_MAX;
-    double sv = ex;
+    float sv = ex.h;  // the nearest FP32 of the exact value
     for (int size = 2; size <= 32; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        const double ok = __shfl_xor_sync(0xffffffffu, key, stride);
+        const dfl ok = df_shfl_xor(key, stride);
         const int oj = __shfl_xor_sync(0xffffffffu, kj, stride);
-        const double os = __shfl_xor_sync(0xffffffffu, sv, stride);
+        const float os = __shfl_xor_sync(0xffffffffu, sv, stride);
         const bool desc = (lane & size) == 0;
         const bool lower = (lane & stride) == 0;
         const bool take_better = lower == desc;
-        const bool self_better = better(key, kj, ok, oj);
+        const bool self_better = df_better(key, kj, ok, oj);
         if (take_better != self_better) key = ok, kj = oj, sv = os;
       }
     }
-    // error bound of the screen for this row
+    // error bound of the screen for this row, rounded up in FP32
     // (sum_k |a_ik| max_j |b_jk|, or ||a_i|| max_j ||b_j|| by Cauchy-Schwarz;
     // colmax_bits[r] holds max_j ||b_j||)
-    double bnd = 0.0, nrm = 0.0;
+    float bsum = 0.f, nsq = 0.f;
     for (int q = lane; q < r; q += 32) {
-      const double aq = vload(V, v64, i * ldv + q) * psi[q];
-      bnd += fabs(aq) * double(__uint_as_float(colmax_bits[q]));
-      nrm += aq * aq;
+      const float vq = v64 ? __double2float_ru(fabs(static_cast<const double*>(V)[i * ldv + q]))
+                           : fabsf(static_cast<const float*>(V)[i * ldv + q]);
+      const float aq = __fmul_ru(vq, psi_up[q]);
+      bsum = __fmaf_ru(aq, __uint_as_float(colmax_bits[q]), bsum);
+      nsq = __fmaf_ru(aq, aq, nsq);
     }
-    bnd = warp_sum(bnd);
-    nrm = sqrt(warp_sum(nrm)) * (1.0 + 1e-12);
-    bnd = fmin(bnd, nrm * double(__uint_as_float(colmax_bits[r]))) * u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bsum = __fadd_ru(bsum, __shfl_xor_sync(0xffffffffu, bsum, o));
+      nsq = __fadd_ru(nsq, __shfl_xor_sync(0xffffffffu, nsq, o));
+    }
+    const float bnd = __fmul_ru(fminf(bsum, __fmul_ru(__fsqrt_ru(nsq), __uint_as_float(colmax_bits[r]))), u_up);
     {
-      double ratio = bnd > 0.0 ? serr / bnd : (serr > 0.0 ? 1e30 : 0.0);
-      ratio = warp_max(ratio);
-      if (lane == 0 && ratio > 0.0) atomicMax(err_bits, __float_as_uint(float(fmin(ratio, 1e30))));
+      float ratio = bnd > 0.f ? serr / bnd : (serr > 0.f ? 1e30f : 0.f);
+      ratio = warp_max_f(ratio);
+      if (lane == 0 && ratio > 0.f) atomicMax(err_bits, __float_as_uint(fminf(ratio, 1e30f)));
     }
-    const double qk = __shfl_sync(0xffffffffu, key, k - 1);
-    const bool certified = t < 0.0 || qk > t + bnd;
+    // certified when the k-th exact value beats every column left out:
+    // those have screened values <= t, exact values <= t + bnd
+    const dfl qk = df_shfl(key, k - 1);
+    const float rhs = __fadd_ru(t, bnd);
+    const bool certified = t < 0.f || qk.h > rhs || (qk.h == rhs && qk.l > 0.f);
     if (lane < k) {
       idx_out[i * k + lane] = kj == INT_MAX ? -1 : kj;
-      val_out[i * k + lane] = float(sv);
+      val_out[i * k + lane] = sv;
     }
     if (!certified && lane == 0) {
       const int pos = atomicAdd(flag_count, 1);
@@ -446,8 +500,11 @@ void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, in
                     const float* thr, int nl, int64_t lstride, int64_t m, const unsigned* colmax_bits, double u,
                     int32_t* idx, float* val, int* flag_list, int* flag_count, unsigned* err_bits) {
   // one warp per row; the grid covers at most m rows (grid-stride beyond)
-  const unsigned blocks = unsigned(std::min<int64_t>((m * 32 + 255) / 256, 65536));
-  rescore_kernel<<<blocks, 256, 0, s>>>(d, r, V, v64, ldv, psi, k, rows, m, count_dev, cidx, cval, thr, nl, lstride,
+  const unsigned blocks = unsigned(std::min<int64_t>((m * 32 + 255) / 256, 4096));
+  const size_t smem = size_t(r) * (sizeof(dfl) + sizeof(float));  // <= 96 KB (r <= 8192)
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  rescore_kernel<<<blocks, 256, smem, s>>>(d, r, V, v64, ldv, psi, k, rows, m, count_dev, cidx, cval, thr, nl, lstride,
                                         colmax_bits, u, idx, val, flag_list, flag_count, err_bits);
 }
 
