@@ -7,8 +7,8 @@
 //   2. multisection with division-free double-float Sturm counts for the
 //      wanted eigenvalues of T (eight lanes per eigenvalue);
 //   3. inverse iteration on T - lambda I (tridiagonal LU with partial
-//      pivoting, one thread per eigenvalue), then modified Gram-Schmidt inside
-//      clusters of nearly equal eigenvalues;
+//      pivoting, one thread per eigenvalue, double-float), then modified
+//      Gram-Schmidt inside clusters of nearly equal eigenvalues;
 //   4. back-transformation Z <- Q Z in compact WY blocks of 32 reflectors
 //      (one cooperative kernel over every SM, one grid barrier per block);
 //   5. output: the r largest eigenvalues descending, vectors row-major d x r.
@@ -363,87 +363,115 @@ __global__ void bisect_kernel(const double* __restrict__ dv_g, const double* __r
   if (active && sub == 0) lam[group] = 0.5 * (lo + hi);
 }
 
-__device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b) {
+// Counter-based hash of (a, b) to [-1, 1], FP32 (the inverse-iteration start).
+__device__ __forceinline__ float hash_unit_f(uint32_t a, uint32_t b) {
   uint32_t x = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
   x ^= x >> 15;
   x *= 0x2C1B3C6Du;
   x ^= x >> 12;
   x *= 0x297A2D39u;
   x ^= x >> 15;
-  return double(x) * (2.0 / 4294967296.0) - 1.0;  // [-1, 1)
+  return __fmaf_rn(__uint2float_rn(x), 0x1p-31f, -1.f);
 }
 
 // Inverse iteration: thread t (eigenvalue lam[t]) solves (T - lam I) z = y
-// three times from a pseudo-random start.  Work arrays are interleaved
-// [i][t] (stride B) so that a warp's accesses coalesce; z ends in Z[i*B + t].
+// kInvIters times from a pseudo-random start, in double-float on c T (c a
+// power of two with ||c T|| about 1; the block's copy in shared memory):
+// each step's quotient and updates are a few dozen FP32 operations instead
+// of an FP64 division on a pipe that issues about one lane per clock.  Work
+// arrays are interleaved [i][t] (stride B) so that a warp's accesses
+// coalesce; z ends, normalised, in Z[i*B + t] as FP64 (the same 8 bytes
+// that held the double-float iterate).
 __global__ void inverse_iter_kernel(const double* __restrict__ dv, const double* __restrict__ ev, int n,
                                     const double* __restrict__ lam, int cnt, int B,
-                                    const double* __restrict__ info, double* __restrict__ u0,
-                                    double* __restrict__ u1, double* __restrict__ u2,
-                                    double* __restrict__ Z, int seed_base) {
+                                    const double* __restrict__ info, dfl* __restrict__ u0, dfl* __restrict__ u1,
+                                    dfl* __restrict__ u2, double* __restrict__ Zd, int seed_base) {
+  extern __shared__ dfl inv_sm[];
+  dfl* sd = inv_sm;      // c T's diagonal
+  dfl* se = inv_sm + n;  // c T's off-diagonal (0 past the end)
+  int ce = 0;
+  {
+    const double tn = info[3];
+    if (tn > 0.0 && isfinite(tn)) frexp(tn, &ce);
+  }
+  const double cs = ldexp(1.0, -ce);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = df_from(dv[i] * cs);
+    se[i] = i + 1 < n ? df_from(ev[i] * cs) : df_zero();
+  }
+  __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
-  const double lm = lam[t];
-  const double nrm = fmax(info[3], DBL_MIN);
-  const double tiny = DBL_EPSILON * nrm;
-  for (int i = 0; i < n; ++i) Z[int64_t(i) * B + t] = hash_unit(uint32_t(seed_base + t), uint32_t(i));
+  dfl* Z = reinterpret_cast<dfl*>(Zd);
+  const dfl nlm = df_from(-lam[t] * cs);
+  const float tiny = 0x1p-52f * float(fmax(info[3], DBL_MIN) * cs);
+  for (int i = 0; i < n; ++i) Z[int64_t(i) * B + t] = dfl{hash_unit_f(uint32_t(seed_base + t), uint32_t(i)), 0.f};
   for (int iter = 0; iter < kInvIters; ++iter) {
     // factor with partial pivoting while applying L^-1 to the right-hand side
-    double a = dv[0] - lm, b = n > 1 ? ev[0] : 0.0;
-    double y = Z[t];  // current y_i (after elimination of previous rows)
+    dfl a = df_add(sd[0], nlm), b = se[0];
+    dfl y = Z[t];  // current y_i (after elimination of previous rows)
     for (int i = 0; i + 1 < n; ++i) {
-      const double c = ev[i];
-      const double na = dv[i + 1] - lm;
-      const double nb = i + 2 < n ? ev[i + 1] : 0.0;
-      const double ynext = Z[int64_t(i + 1) * B + t];
-      double yi, ynew;
-      if (fabs(a) >= fabs(c)) {
-        const double piv = fabs(a) < tiny ? (a < 0.0 ? -tiny : tiny) : a;
-        const double l = c / piv;
-        u0[int64_t(i) * B + t] = piv;
-        u1[int64_t(i) * B + t] = b;
-        u2[int64_t(i) * B + t] = 0.0;
+      const dfl c = se[i];
+      const dfl na = df_add(sd[i + 1], nlm);
+      const dfl nb = se[i + 1 < n ? i + 1 : i];
+      const dfl nbv = i + 2 < n ? nb : df_zero();
+      const dfl ynext = Z[int64_t(i + 1) * B + t];
+      dfl yi, ynew;
+      const int64_t o = int64_t(i) * B + t;
+      if (fabsf(a.h) >= fabsf(c.h)) {
+        const dfl piv = fabsf(a.h) < tiny ? dfl{a.h < 0.f ? -tiny : tiny, 0.f} : a;
+        const dfl nl = df_neg(df_div(c, piv));
+        u0[o] = piv;
+        u1[o] = b;
+        u2[o] = df_zero();
         yi = y;
-        ynew = ynext - l * y;
-        a = na - l * b;
-        b = nb;
+        ynew = df_fma(ynext, nl, y);  // ynext - l y
+        a = df_fma(na, nl, b);        // na - l b
+        b = nbv;
       } else {
-        const double l = a / c;
-        u0[int64_t(i) * B + t] = c;
-        u1[int64_t(i) * B + t] = na;
-        u2[int64_t(i) * B + t] = nb;
+        const dfl nl = df_neg(df_div(a, c));
+        u0[o] = c;
+        u1[o] = na;
+        u2[o] = nbv;
         yi = ynext;
-        ynew = y - l * ynext;
-        a = b - l * na;
-        b = -l * nb;
+        ynew = df_fma(y, nl, ynext);  // y - l ynext
+        a = df_fma(b, nl, na);        // b - l na
+        b = df_mul(nl, nbv);          // -l nb
       }
-      Z[int64_t(i) * B + t] = yi;
+      Z[o] = yi;
       y = ynew;
     }
-    const double last = fabs(a) < tiny ? (a < 0.0 ? -tiny : tiny) : a;
+    const dfl last = fabsf(a.h) < tiny ? dfl{a.h < 0.f ? -tiny : tiny, 0.f} : a;
     // back substitution, tracking the largest magnitude for scaling
-    double z2 = 0.0, z1 = y / last;
+    dfl z2 = df_zero(), z1 = df_div(y, last);
     Z[int64_t(n - 1) * B + t] = z1;
-    double zmax = fabs(z1);
+    float zmax = fabsf(z1.h);
     for (int i = n - 2; i >= 0; --i) {
-      const double zi = (Z[int64_t(i) * B + t] - u1[int64_t(i) * B + t] * z1 - u2[int64_t(i) * B + t] * z2) /
-                        u0[int64_t(i) * B + t];
-      Z[int64_t(i) * B + t] = zi;
+      const int64_t o = int64_t(i) * B + t;
+      const dfl zi = df_div(df_sub2(Z[o], u1[o], z1, u2[o], z2), u0[o]);
+      Z[o] = zi;
       z2 = z1;
       z1 = zi;
-      zmax = fmax(zmax, fabs(zi));
+      zmax = fmaxf(zmax, fabsf(zi.h));
     }
-    // scale (keeps the next solve in range) and, on the last pass, normalise
-    double s = 1.0 / fmax(zmax, DBL_MIN);
-    if (iter == kInvIters - 1) {
-      double nn = 0.0;
+    // scale (keeps the next solve in range); on the last pass normalise and
+    // write FP64
+    const dfl sc{1.f / fmaxf(zmax, FLT_MIN), 0.f};
+    if (iter + 1 < kInvIters) {
+      for (int i = 0; i < n; ++i) Z[int64_t(i) * B + t] = df_mul(Z[int64_t(i) * B + t], sc);
+    } else {
+      dfl nn = df_zero();
       for (int i = 0; i < n; ++i) {
-        const double zi = Z[int64_t(i) * B + t] * s;
-        nn += zi * zi;
+        const dfl zi = df_mul(Z[int64_t(i) * B + t], sc);
+        nn = df_fma(nn, zi, zi);
       }
-      s = s / sqrt(nn);
+      const dfl s2 = df_div(sc, df_sqrt(nn));
+      for (int i = 0; i < n; ++i) {
+        const int64_t o = int64_t(i) * B + t;
+        const dfl zi = df_mul(Z[o], s2);
+        Zd[o] = df_val(zi);
+      }
     }
-    for (int i = 0; i < n; ++i) Z[int64_t(i) * B + t] *= s;
   }
 }
 
@@ -778,10 +806,15 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
       ++launches;
     }
     const int B = std::min(nvec, kInvBatch);
+    const size_t ismem = size_t(2) * n * sizeof(dfl);
+    if ((e = cudaFuncSetAttribute(inverse_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem))) !=
+        cudaSuccess)
+      return e;
     for (int t0 = 0; t0 < nvec; t0 += B) {
       const int cnt = std::min(B, nvec - t0);
-      inverse_iter_kernel<<<unsigned((cnt + 31) / 32), 32, 0, st>>>(s.dv, s.ev, n, lamv + t0, cnt, B, s.info,
-                                                                     s.u0, s.u1, s.u2, s.Z, t0);
+      inverse_iter_kernel<<<unsigned((cnt + 31) / 32), 32, ismem, st>>>(
+          s.dv, s.ev, n, lamv + t0, cnt, B, s.info, reinterpret_cast<dfl*>(s.u0), reinterpret_cast<dfl*>(s.u1),
+          reinterpret_cast<dfl*>(s.u2), s.Z, t0);
       dim3 tb(32, 8), tg(unsigned((cnt + 31) / 32), unsigned((n + 31) / 32));
       transpose_kernel<<<tg, tb, 0, st>>>(s.Z, n, cnt, B, s.Zc, t0);
       launches += 2;
