@@ -26,6 +26,7 @@ __global__ void colsum_log1p_kernel(const float* __restrict__ c, int64_t n, int6
   if (col >= p) return;
   float s = 0.f, comp = 0.f;
   const float* src = c + r0 * ldc + col;
+#pragma unroll 8
   for (int64_t r = r0; r < r1; ++r, src += ldc) {
     float y = log1pf(__ldg(src)) - comp;
     float t = s + y;
