@@ -86,6 +86,21 @@ __device__ __forceinline__ void householder(dfl* x, int m, dfl* red, dfl& tau, d
   __syncthreads();
 }
 
+// The scalars of the Householder reflector of x = (x0, x1..): tau, beta and
+// the scale sc of x1.. (v = (1, sc x1, ...)), from x0 and the squared tail
+// sum_{i>=1} x_i^2.  False when the tail is zero (tau = 0, no scaling).
+__device__ __forceinline__ bool reflector_scalars(dfl x0, dfl tail, dfl& tau, dfl& beta, dfl& sc) {
+  tau = df_zero();
+  beta = x0;
+  sc = dfl{1.f, 0.f};
+  if (!(tail.h > 0.f)) return false;
+  const dfl nrm = df_sqrt(df_fma(tail, x0, x0));
+  beta = x0.h >= 0.f ? df_neg(nrm) : nrm;
+  tau = df_div(df_add(beta, df_neg(x0)), beta);
+  sc = df_div(dfl{1.f, 0.f}, df_add(x0, df_neg(beta)));
+  return true;
+}
+
 // Tridiagonalisation with one grid barrier per reflector: the rank-2 update
 // of step k and the mat-vec of step k+1 share one pass over the trailing
 // matrix.  Row k+1 of the updated matrix (which defines reflector k+1) is
@@ -148,55 +163,70 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
     }
     if (!grid_barrier(bar, nb, status)) return;
   }
+  // Reflector k lives at vb (vb[0] == 1); row k+1 and then reflector k+1 are
+  // formed in the other buffer ub, so the next reflector is ub + 1 and the
+  // buffer of the current one takes the next row: no copy.
+  __shared__ dfl xs0;  // entry k+2 of the updated row k+1 (x0 of reflector k+1)
+  dfl* vb = v;
+  dfl* ub = u;
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;  // size of the trailing block of step k
-    // w = P - K v, K = tau_k (P.v) / 2
     const dfl* Pc = P + (k & 1) * int64_t(n);
     dfl* Pn = P + ((k + 1) & 1) * int64_t(n);
+    const float2* rowk = reinterpret_cast<const float2*>(A) + int64_t(k + 1) * n + k + 1;
+    // one round trip to L2: P into w, row k+1 of the old matrix into ub
+    const float2 p0 = __ldcg(reinterpret_cast<const float2*>(Pc));
     dfl pv = df_zero();
 #pragma unroll 4
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const float2 pc = __ldcg(reinterpret_cast<const float2*>(Pc) + i);
+      const float2 a = __ldcg(rowk + i);
       w[i] = dfl{pc.x, pc.y};
-      pv = df_fma(pv, w[i], v[i]);
+      ub[i] = dfl{a.x, a.y};
+      pv = df_fma(pv, w[i], vb[i]);
     }
     const bool live = tk.h != 0.f;  // reflector k is not the identity
     const dfl nK = df_mul(dfl{-0.5f * tk.h, -0.5f * tk.l}, df_block_sum(pv, red));  // -tau_k (P.v) / 2
-    for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = live ? df_fma(w[i], nK, v[i]) : df_zero();
-    __syncthreads();
-    // row k+1 of the updated matrix, columns k+1..n-1 -> u[0..m-1]
-    {
-      const float2* row = reinterpret_cast<const float2*>(A) + int64_t(k + 1) * n + k + 1;
-      const dfl v0 = v[0], w0 = w[0];
-#pragma unroll 4
-      for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const float2 a = __ldcg(row + j);
-        u[j] = df_sub2(dfl{a.x, a.y}, v0, w[j], w0, v[j]);
-      }
+    // w = P - K v, the updated row k+1 (u = row - v0 w - w0 v) and the
+    // squared tail of reflector k+1's x = u[1..]; each thread touches its
+    // own indices of w and ub
+    const dfl v0 = vb[0];
+    const dfl w0 = live ? df_fma(dfl{p0.x, p0.y}, nK, v0) : df_zero();
+    dfl ss = df_zero();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const dfl wi = live ? df_fma(w[i], nK, vb[i]) : df_zero();
+      w[i] = wi;
+      const dfl ui = df_sub2(ub[i], v0, wi, w0, vb[i]);
+      ub[i] = ui;
+      if (i >= 2) ss = df_fma(ss, ui, ui);
+      if (i == 1) xs0 = ui;
     }
-    __syncthreads();
-    const dfl dnext = u[0];
-    dfl tn = df_zero(), bn;
+    const dfl tail = df_block_sum(ss, red);  // ub, w and xs0 complete after its barriers
+    const dfl dnext = ub[0];
+    dfl tn = df_zero(), bn = xs0;
     const bool more = k + 3 < n;  // a reflector k+1 exists
     if (more) {
-      householder(u + 1, m - 1, red, tn, bn);  // u+1 holds x = row entries k+2..n-1
-    } else {
-      bn = u[1];
+      dfl sc;
+      if (reflector_scalars(xs0, tail, tn, bn, sc))
+        for (int i = 2 + threadIdx.x; i < m; i += blockDim.x) ub[i] = df_mul(ub[i], sc);
+      if (threadIdx.x == 0) ub[1] = dfl{1.f, 0.f};
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       dv[k + 1] = df_val(dnext) * unscale;
       ev[k + 1] = df_val(bn) * unscale;
       if (more) tau_out[k + 1] = df_val(tn);
     }
+    __syncthreads();
+    const dfl* uu = ub;  // u[1..]: reflector k+1
     if (more)
-      for (int i = gthread; i < m - 1; i += total_threads) Vh[int64_t(k + 1) * n + k + 2 + i] = df_val(u[1 + i]);
+      for (int i = gthread; i < m - 1; i += total_threads) Vh[int64_t(k + 1) * n + k + 2 + i] = df_val(uu[1 + i]);
     // fused pass: rows i, cols j in k+2..n-1 (local index t = i - (k+1) >= 1)
     const bool upd = live;
     const dfl tnd = tn;
     for (int it = gwarp; it < (m - 1); it += total_warps) {
       const int t = 1 + it;
       float2* row = reinterpret_cast<float2*>(A) + int64_t(k + 1 + t) * n + k + 2;
-      const dfl vi = v[t], wi = w[t];
+      const dfl vi = vb[t], wi = w[t];
       const int mm = m - 1;
       dfl acc[kBatch];
 #pragma unroll
@@ -219,10 +249,10 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
           if (jj < mm) {
             dfl x{a[q].x, a[q].y};
             if (upd) {
-              x = df_sub2(x, vi, w[1 + jj], wi, v[1 + jj]);
+              x = df_sub2(x, vi, w[1 + jj], wi, vb[1 + jj]);
               row[jj] = make_float2(x.h, x.l);
             }
-            acc[q] = df_fma(acc[q], x, u[1 + jj]);
+            acc[q] = df_fma(acc[q], x, uu[1 + jj]);
           }
         }
 #pragma unroll
@@ -233,9 +263,11 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
       const dfl s = df_warp_sum(acc[0]);
       if (lane == 0 && more) Pn[it] = df_mul(tnd, s);
     }
-    // next step's reflector (after every warp of the CTA is done reading v, w)
-    __syncthreads();
-    for (int i = threadIdx.x; i < m - 1; i += blockDim.x) v[i] = u[1 + i];
+    // the next reflector is ub + 1; the current one's buffer takes row k+2
+    // (every read of vb, w and ub ends before the barrier's first sync)
+    dfl* const base_v = vb == v || vb == v + 1 ? v : u;
+    vb = ub + 1;
+    ub = base_v;
     tk = tn;
     if (!grid_barrier(bar, nb, status)) return;
   }
