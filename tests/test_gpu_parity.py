@@ -134,6 +134,37 @@ def test_spectra_degenerate_and_clustered(g, cuda_dev):
     _check_eig(S, ev.cpu().numpy(), W.cpu().numpy(), 30)
 
 
+@pytest.mark.parametrize("case", ["logspace", "scaled_up", "scaled_down", "d4000"])
+def test_spectra_range_and_scaling(g, cuda_dev, case):
+    # the reduction runs in double-float on a power-of-two-scaled copy:
+    # eigenvalues spread over twelve decades, Grams scaled by 2^+-100
+    # (far outside the FP32 range before scaling) and a 4000 x 4000 Gram
+    # must still match the oracle to FP64-like accuracy
+    rng = _rng(12)
+    if case == "logspace":
+        d = 600
+        q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+        S = (q * np.logspace(-6, 6, d)) @ q.T
+    elif case == "d4000":
+        d = 4000
+        x = rng.standard_normal((d + 50, d))
+        S = x.T @ x
+    else:
+        d = 500
+        x = rng.standard_normal((d + 50, d))
+        S = (x.T @ x) * (2.0 ** (100 if case == "scaled_up" else -100))
+    S = 0.5 * (S + S.T)
+    r = 40
+    ev, W = g.spectra(torch.from_numpy(S).to(cuda_dev), d, rv=r)
+    ev = ev.cpu().numpy()
+    W = W.cpu().numpy()
+    e_ref, _ = osp.top_eigh(S, d)
+    scale = np.abs(e_ref).max()
+    np.testing.assert_allclose(ev, e_ref, rtol=0, atol=1e-11 * scale)
+    assert np.max(np.abs(S @ W - W * ev[None, :r])) <= 1e-10 * scale
+    assert np.max(np.abs(W.T @ W - np.eye(r))) <= 1e-8
+
+
 def test_lift_matches_oracle(g, cuda_dev):
     x, _, _ = planted_c1()
     x = (x - x.mean(0)).astype(np.float32)
