@@ -58,28 +58,28 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // Spin limit for grid barriers: ~2^26 polls (a few seconds at most).
 constexpr long long kBarrierSpinLimit = 1ll << 26;
 
-// Sense-reversing grid barrier for a cooperative launch (all CTAs resident).
-// bar[0] = arrivals, bar[1] = generation, bar[2] = abort flag.  Every wait is
-// bounded: on timeout the TIMEOUT status bit and the abort flag are set and
-// the function returns false; callers then leave the kernel.  Once aborted,
-// every later call returns false immediately.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+// Grid barrier for a cooperative launch (all CTAs resident), on a counter
+// of arrivals that only grows during the launch: bar[0] = arrivals (zeroed
+// before the launch), bar[2] = abort flag.  `epoch` counts the barriers this
+// CTA has passed (every CTA passes the same ones), so barrier e completes
+// when bar[0] reaches (e + 1) * nblocks: one atomic per CTA and no reset or
+// generation word on the critical path.  Every wait is bounded: on timeout
+// the TIMEOUT status bit and the abort flag are set and the function
+// returns false; callers then leave the kernel.  Once aborted, every later
+// call returns false immediately.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& epoch, int* status) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vb = bar;
     int ok = vb[2] == 0u;
     if (ok) {
-      unsigned gen = vb[1];
-      __threadfence();
-      unsigned arrived = atomicAdd(&bar[0], 1u);
-      if (arrived == nblocks - 1) {
-        bar[0] = 0u;
-        __threadfence();
-        atomicAdd(&bar[1], 1u);
-      } else {
+      const unsigned target = (epoch + 1u) * nblocks;
+      __threadfence();  // this CTA's writes (ordered before by the CTA barrier) before the arrival
+      const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+      if (arrived != target) {
         long long spins = 0;
-        while (vb[1] == gen) {
+        while (static_cast<int>(vb[0] - target) < 0) {
           if (vb[2] != 0u || ++spins > kBarrierSpinLimit) {
             ok = 0;
             break;
@@ -95,6 +95,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
     }
     ok_s = ok;
   }
+  ++epoch;
   __syncthreads();
   return ok_s != 0;
 }

@@ -14,7 +14,7 @@ struct gmgm_handle {
   int num_sms = 0;
   // device status word (OR of GMGM_DEV_* bits) + grid-barrier words
   int* d_status = nullptr;
-  unsigned* d_barrier = nullptr;  // [0] = arrive count, [1] = generation
+  unsigned* d_barrier = nullptr;  // [0] = arrivals in the current launch, [2] = abort flag
   // lazily grown scratch arena
   void* scratch = nullptr;
   size_t scratch_bytes = 0;

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
   const int gwarp = blockIdx.x * nwarps + warp, total_warps = nb * nwarps;
   const int gthread = blockIdx.x * blockDim.x + threadIdx.x, total_threads = nb * blockDim.x;
   const double unscale = ldexp(1.0, scale_exp(amax));
+  unsigned epoch = 0;  // grid barriers passed
   // prologue: reflector 0 from row 0, P = tau_0 A[1:,1:] v
   dfl tk, beta;
   {
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
       const dfl s = df_warp_sum(acc[0]);
       if (lane == 0) P[i] = df_mul(td, s);
     }
-    if (!grid_barrier(bar, nb, status)) return;
+    if (!grid_barrier(bar, nb, epoch, status)) return;
   }
   // Reflector k lives at vb (vb[0] == 1); row k+1 and then reflector k+1 are
   // formed in the other buffer ub, so the next reflector is ub + 1 and the
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
     vb = ub + 1;
     ub = base_v;
     tk = tn;
-    if (!grid_barrier(bar, nb, status)) return;
+    if (!grid_barrier(bar, nb, epoch, status)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const float2 a = __ldcg(reinterpret_cast<const float2*>(A) + int64_t(n - 1) * n + n - 1);
@@ -644,6 +645,7 @@ __global__ void __launch_bounds__(256) wy_apply_kernel(const double* __restrict_
   double* Us = Vs + kWY * chunk;          // [kWY][chunk]
   double* Ys = Us + kWY * chunk;          // [kWY][kWYV]
   const unsigned nb = gridDim.x;
+  unsigned epoch = 0;  // grid barriers passed
   const int r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
   const int rows = max(0, r1 - r0);
   const int ngroups = (cnt + kWYV - 1) / kWYV;
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(256) wy_apply_kernel(const double* __restrict_
           atomicAdd(Yb + j * kWYV + c, s);
         }
       }
-      if (!grid_barrier(bar, nb, status)) return;
+      if (!grid_barrier(bar, nb, epoch, status)) return;
       if (lo < rows) {
         for (int e = threadIdx.x; e < kWY * nv; e += blockDim.x) {
           const int j = e / nv, c = e - j * nv;
