@@ -5,7 +5,7 @@
 //      pairs, the matrix scaled by a power of two), one cooperative kernel
 //      with one bounded grid barrier per reflector (matrix in L2);
 //   2. multisection with division-free double-float Sturm counts for the
-//      wanted eigenvalues of T (eight lanes per eigenvalue);
+//      wanted eigenvalues of T (sixteen lanes per eigenvalue);
 //   3. inverse iteration on T - lambda I (tridiagonal LU with partial
 //      pivoting, one thread per eigenvalue, double-float), then modified
 //      Gram-Schmidt inside clusters of nearly equal eigenvalues;
@@ -346,7 +346,7 @@ __device__ __forceinline__ int sturm_count_df(const dfl* dv, const dfl* e2, int 
   return cnt;
 }
 
-constexpr int kBisectLanes = 8;  // lanes per eigenvalue ((lanes + 1)-way multisection)
+constexpr int kBisectLanes = 16;  // lanes per eigenvalue ((lanes + 1)-way multisection)
 
 // Lanes in groups of kMS find the ascending eigenvalues j0 + group (or
 // jlist[group]): each round evaluates kMS interior points of the current
