@@ -27,6 +27,11 @@ Each function cites the part of the paper it follows:
                    definition; the model equation; appendix on the singular
                    distribution).
 * ``mlp``       -- FP64 forward/backward of the warm-start network.
+* ``skeptic``   -- rank-based statistics: per-row minimum ranks, normal
+                   scores Phi^-1(rank / (n + 1)) and their Gram (Section "The
+                   model", the Nonparanormal Skeptic; Section "Algorithm",
+                   the COCA form; the worked example of the appendix on
+                   preserving input sparsity).
 
 Pins live in ``tests/test_oracle_*.py`` (``-m "not gpu"``).
 """
