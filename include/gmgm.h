@@ -98,6 +98,18 @@ const char* gmgm_last_error(const gmgm_handle* h);
  * value is a gmgm_status for a failed synchronisation. */
 int gmgm_device_status(gmgm_handle* h);
 
+/* Failure-detection check: one kernel polls a device word that nothing
+ * sets, `spins` times (1 <= spins <= 2^20, about 100 ns apart), then sets
+ * GMGM_DEV_TIMEOUT and returns, the path every spinning kernel of the
+ * library takes when a bounded wait gives up.  Enqueued on the handle's
+ * stream; read the bit with gmgm_device_status.  The handle stays usable.
+ * Errors: GMGM_E_ARG for spins out of range.
+ *
+ * Host-side fault injection: with the environment variable GMGM_FAULT
+ * containing "alloc", every call whose scratch has to grow returns
+ * GMGM_E_NOMEM instead of allocating (nothing is faulted on the device). */
+int gmgm_probe_wait(gmgm_handle* h, int64_t spins);
+
 /* Library version string, e.g. "gmgm 0.1 sm_103a". */
 const char* gmgm_version(void);
 

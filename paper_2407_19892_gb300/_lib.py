@@ -76,6 +76,7 @@ SIGNATURES = {
     "gmgm_set_stream": (c_int, [c_vp, c_vp]),
     "gmgm_last_error": (ctypes.c_char_p, [c_vp]),
     "gmgm_device_status": (c_int, [c_vp]),
+    "gmgm_probe_wait": (c_int, [c_vp, c_i64]),
     "gmgm_version": (ctypes.c_char_p, []),
     "gmgm_kernel_launches": (ctypes.c_uint64, []),
     "gmgm_preprocess": (c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp,

@@ -65,6 +65,11 @@ class Handle:
             self.check(rc)
         return rc
 
+    def probe_wait(self, spins):
+        """Enqueue the bounded-wait check (gmgm_probe_wait): a wait on a flag
+        nothing sets gives up after `spins` polls and sets the TIMEOUT bit."""
+        self.check(self.lib.gmgm_probe_wait(self.h, int(spins)))
+
 
 _default = {}
 

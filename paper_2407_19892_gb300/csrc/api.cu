@@ -2,9 +2,11 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
+#include "device.cuh"
 #include "internal.cuh"
 
 namespace gmgm {
@@ -18,8 +20,30 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void note_launch(int n) { g_launches.fetch_add(static_cast<unsigned long long>(n), std::memory_order_relaxed); }
 
+// Host-side fault injection: GMGM_FAULT holds a comma-separated list of
+// injected failures ("alloc": a scratch allocation that has to grow fails).
+// The failure is produced on the host; nothing is faulted on the device.
+bool fault_injected(const char* what) {
+  const char* f = std::getenv("GMGM_FAULT");
+  return f && std::strstr(f, what);
+}
+
+// A bounded wait on a device word that nothing sets: after `spins` polls
+// the TIMEOUT status bit is set and the kernel returns (the path every
+// spinning kernel takes when a wait gives up).
+__global__ void probe_wait_kernel(const unsigned* flag, long long spins, int* status) {
+  if (threadIdx.x != 0) return;
+  const volatile unsigned* f = flag;
+  for (long long i = 0; i < spins; ++i) {
+    if (*f != 0u) return;
+    __nanosleep(100);
+  }
+  set_status(status, GMGM_DEV_TIMEOUT);
+}
+
 int ensure_scratch(gmgm_handle* h, size_t bytes) {
   if (bytes <= h->scratch_bytes) return GMGM_OK;
+  if (fault_injected("alloc")) return fail(h, GMGM_E_NOMEM, "scratch allocation failed (injected: GMGM_FAULT=alloc)");
   if (h->scratch) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->scratch);
@@ -108,6 +132,17 @@ int gmgm_device_status(gmgm_handle* h) {
   GMGM_CUDA_TRY(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   GMGM_CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(int)));
   return st;
+}
+
+int gmgm_probe_wait(gmgm_handle* h, int64_t spins) {
+  if (!h) return GMGM_E_ARG;
+  if (spins < 1 || spins > (int64_t(1) << 20)) return fail(h, GMGM_E_ARG, "gmgm_probe_wait: need 1 <= spins <= 2^20");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  unsigned* flag = h->d_barrier + 8;  // a word no kernel writes
+  GMGM_CUDA_TRY(h, cudaMemsetAsync(flag, 0, sizeof(unsigned), h->stream));
+  gmgm::probe_wait_kernel<<<1, 32, 0, h->stream>>>(flag, spins, h->d_status);
+  GMGM_CUDA_TRY(h, cudaGetLastError());
+  return GMGM_OK;
 }
 
 int gmgm_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc,

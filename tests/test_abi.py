@@ -43,6 +43,8 @@ def test_null_handle_is_an_argument_error(lib):
     assert lib.gmgm_device_status(None) == -1
     lib.gmgm_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.gmgm_version()
+    lib.gmgm_probe_wait.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert lib.gmgm_probe_wait(None, 10) == -1
 
 
 def test_struct_layouts_match_header(tmp_path):
