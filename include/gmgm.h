@@ -409,7 +409,8 @@ typedef struct {
  * Exactness: every row's screen is certified with a rigorous error bound of
  * the screen arithmetic (the k-th exact value must beat the best excluded
  * screened value plus the bound, rounded up); rows that fail are rescreened
- * with split products and, failing again, recomputed in FP64, so idx_out is
+ * with split products (after a BF16 screen) and, failing again, recomputed
+ * in FP64, so idx_out is
  * the exact top-k of the given V and psi.  Candidates are ranked by values
  * exact to about 2^-46 of sum_q |V_iq psi_q V_jq|: entries closer than that
  * may be ordered either way (equal values by the lower column).
