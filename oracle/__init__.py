@@ -20,8 +20,9 @@ Each function cites the part of the paper it follows:
                    gradient; the elementwise form in the existence lemma;
                    Algorithm 1's gradient step), by a projected Newton method,
                    plus the paper's literal gradient iteration.
-* ``recon``     -- Psi_l = V_l diag(Lam_l) V_l^T and its per-row top-k
-                   (Algorithm 1, last loop: threshold with recomposition).
+* ``recon``     -- Psi_l = V_l diag(Lam_l) V_l^T, its per-row top-k and the
+                   global top-n edges (Algorithm 1, last loop: threshold with
+                   recomposition; the complexity appendix's heap of size n_l).
 * ``kron``      -- Kronecker sums and the dense (brute-force) likelihood used to
                    pin the rest on tiny problems (Introduction's Kronecker-sum
                    definition; the model equation; appendix on the singular

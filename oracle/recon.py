@@ -69,3 +69,64 @@ def topk_gap(v: np.ndarray, lam: np.ndarray, k: int, rows=None, block: int = 256
             else:
                 gap[b0 + t] = np.inf
     return gap
+
+
+def _edge_order(mag: np.ndarray, i: np.ndarray, j: np.ndarray) -> np.ndarray:
+    """Indices sorting edges by |value| descending, then (i, j) ascending."""
+    return np.lexsort((j, i, -mag))
+
+
+def topn_edges(v: np.ndarray, lam: np.ndarray, n: int, block: int = 256):
+    """The n strongest edges of Psi = V diag(lam) V^T over unordered pairs
+    i < j: the global threshold thresh_{n_l} of Algorithm 1's last loop
+    (the complexity appendix keeps it with a heap of size n_l).  Returns
+    (i, j, value) arrays sorted by |value| descending, ties by (i, j)
+    ascending.  Row blocks of Psi are formed exactly in FP64."""
+    v = np.asarray(v, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    d = v.shape[0]
+    if not 0 < n <= d * (d - 1) // 2:
+        raise ValueError("need 0 < n <= d (d - 1) / 2")
+    vl = v * lam[None, :]
+    bi = np.empty(0, np.int64)
+    bj = np.empty(0, np.int64)
+    bv = np.empty(0)
+    for r0 in range(0, d, block):
+        rows = np.arange(r0, min(d, r0 + block))
+        psi = vl[rows] @ v.T
+        ii, jj = np.nonzero(np.arange(d)[None, :] > rows[:, None])
+        ci = rows[ii]
+        cv = psi[ii, jj]
+        bi, bj, bv = np.concatenate([bi, ci]), np.concatenate([bj, jj]), np.concatenate([bv, cv])
+        keep = _edge_order(np.abs(bv), bi, bj)[:n]
+        bi, bj, bv = bi[keep], bj[keep], bv[keep]
+    return bi, bj, bv
+
+
+def topn_from_row_lists(idx: np.ndarray, val: np.ndarray, n: int):
+    """Global top-n edges from per-row top-k lists (idx, val: d x k, row i
+    holding its k strongest off-diagonal entries, as ``topk_rows`` returns
+    them): the union of the lists as unordered pairs, its n strongest in the
+    order of ``topn_edges``, and whether that is certified to be the global
+    top-n.  It is when every row's k-th magnitude lies strictly below the
+    n-th magnitude of the union (no row can then hold an edge that strong
+    outside its own list), or when every list holds all d - 1 columns.
+    Returns (i, j, value, certified)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    val = np.asarray(val, dtype=np.float64)
+    d, k = idx.shape
+    rows = np.repeat(np.arange(d), k)
+    cols = idx.ravel()
+    vals = val.ravel()
+    i = np.minimum(rows, cols)
+    j = np.maximum(rows, cols)
+    _, first = np.unique(i * d + j, return_index=True)  # each pair once
+    i, j, vals = i[first], j[first], vals[first]
+    order = _edge_order(np.abs(vals), i, j)[:n]
+    i, j, vals = i[order], j[order], vals[order]
+    if len(vals) < n:
+        return i, j, vals, False
+    if k == d - 1:
+        return i, j, vals, True
+    kth = np.abs(val[:, k - 1])
+    return i, j, vals, bool(np.all(kth < abs(vals[-1])))

@@ -3,7 +3,9 @@
 import heapq
 
 import numpy as np
+import pytest
 
+from oracle import recon
 from oracle.recon import recompose, topk_gap, topk_rows
 from oracle.fit import fit_two_axis
 from synth import planted_c1
@@ -92,3 +94,73 @@ def test_planted_recovery_sanity_c1():
     prec = hits / (2 * 100)
     density = true.sum() / (100 * 99)
     assert prec > 2 * density  # about 3x chance from one 200 x 100 draw
+
+
+# ---- global top-n (the paper's heap of n_l edges) -----------------------------
+
+def _brute_topn(V, lam, n):
+    psi = recon.recompose(V, lam)
+    d = psi.shape[0]
+    edges = [(-abs(psi[i, j]), i, j, psi[i, j]) for i in range(d) for j in range(i + 1, d)]
+    edges.sort()
+    top = edges[:n]
+    return (np.array([e[1] for e in top]), np.array([e[2] for e in top]), np.array([e[3] for e in top]))
+
+
+@pytest.mark.parametrize("block", [1, 4, 256])
+def test_topn_edges_is_the_sorted_pair_list(block):
+    rng = np.random.default_rng(11)
+    V = rng.standard_normal((25, 4))
+    lam = rng.uniform(0.5, 2.0, 4)
+    i, j, v = recon.topn_edges(V, lam, 37, block=block)
+    bi, bj, bv = _brute_topn(V, lam, 37)
+    assert np.array_equal(i, bi) and np.array_equal(j, bj)
+    np.testing.assert_allclose(v, bv, rtol=1e-13, atol=1e-13)
+
+
+def test_topn_edges_orders_ties_by_pair():
+    # duplicated rows: equal magnitudes, ordered by (i, j)
+    rng = np.random.default_rng(12)
+    V = np.repeat(rng.standard_normal((6, 3)), 3, axis=0)
+    lam = rng.uniform(0.5, 1.5, 3)
+    i, j, v = recon.topn_edges(V, lam, 40)
+    bi, bj, bv = _brute_topn(V, lam, 40)
+    assert np.array_equal(i, bi) and np.array_equal(j, bj)
+
+
+def test_topn_from_row_lists_certified_equals_global():
+    rng = np.random.default_rng(13)
+    V = rng.standard_normal((80, 6))
+    lam = rng.uniform(0.5, 2.0, 6)
+    idx, val = recon.topk_rows(V, lam, 10)
+    i, j, v, ok = recon.topn_from_row_lists(idx, val, 40)
+    assert ok
+    gi, gj, gv = recon.topn_edges(V, lam, 40)
+    assert np.array_equal(i, gi) and np.array_equal(j, gj)
+    np.testing.assert_allclose(v, gv, rtol=1e-12)
+
+
+def test_topn_from_row_lists_refuses_a_clique_its_lists_cannot_hold():
+    # a 12-node clique of strong edges: with 5 slots per row at most 60 of its
+    # 66 edges reach the union, so the derivation must not claim the top 66.
+    # With 11 slots every clique edge is listed, but a clique row's list is
+    # then all strong and could hide a 12th: still not certified.  With 12
+    # slots each clique row shows one weak entry and it is certified
+    rng = np.random.default_rng(14)
+    d = 40
+    M = 10.0 * np.eye(d) + 0.01 * rng.standard_normal((d, d))
+    M[:12, :12] += 5.0 + 0.1 * rng.standard_normal((12, 12))
+    M = 0.5 * (M + M.T)
+    lam, V = np.linalg.eigh(M)
+    idx, val = recon.topk_rows(V, lam, 5)
+    *_, ok = recon.topn_from_row_lists(idx, val, 66)
+    assert not ok
+    idx, val = recon.topk_rows(V, lam, 11)
+    *_, ok = recon.topn_from_row_lists(idx, val, 66)
+    assert not ok
+    idx, val = recon.topk_rows(V, lam, 12)
+    i, j, v, ok = recon.topn_from_row_lists(idx, val, 66)
+    assert ok
+    gi, gj, _ = recon.topn_edges(V, lam, 66)
+    assert np.array_equal(i, gi) and np.array_equal(j, gj)
+    assert np.all(i < 12) and np.all(j < 12)
