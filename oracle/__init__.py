@@ -28,6 +28,9 @@ Each function cites the part of the paper it follows:
                    definition; the model equation; appendix on the singular
                    distribution).
 * ``mlp``       -- FP64 forward/backward of the warm-start network.
+* ``sparse``    -- the column Gram and the dual lift of log1p(counts) with
+                   centring, from the sparse matrix and rank-one corrections
+                   (the appendix on preserving input sparsity).
 * ``skeptic``   -- rank-based statistics: per-row minimum ranks, normal
                    scores Phi^-1(rank / (n + 1)) and their Gram (Section "The
                    model", the Nonparanormal Skeptic; Section "Algorithm",
