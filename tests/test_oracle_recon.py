@@ -164,3 +164,57 @@ def test_topn_from_row_lists_refuses_a_clique_its_lists_cannot_hold():
     gi, gj, _ = recon.topn_edges(V, lam, 66)
     assert np.array_equal(i, gi) and np.array_equal(j, gj)
     assert np.all(i < 12) and np.all(j < 12)
+
+
+# ---- cone bound for skipping column tiles ---------------------------------------
+
+def test_cone_bound_bounds_every_column_of_the_tile():
+    rng = np.random.default_rng(21)
+    for trial in range(50):
+        r = int(rng.integers(2, 12))
+        centre = rng.standard_normal(r)
+        spread = 10.0 ** rng.uniform(-3, 0.5)
+        b = centre[None, :] + spread * rng.standard_normal((64, r))
+        b *= rng.choice([-1.0, 1.0], size=(64, 1)) * rng.uniform(0.2, 3.0, size=(64, 1))
+        a = rng.standard_normal((40, r)) * rng.uniform(0.1, 10.0, size=(40, 1))
+        c, s, bmax = recon.tile_cone(b)
+        exact = np.max(np.abs(a @ b.T), axis=1)
+        assert np.all(exact <= cone_bound_tol(recon.cone_bound(a, c, s, bmax)))
+
+
+def cone_bound_tol(x):
+    return x * (1.0 + 1e-12) + 1e-300
+
+
+def test_cone_bound_is_attained_for_aligned_and_boundary_columns():
+    # two columns of norm 2 at angle t: the cone's centre is their bisector,
+    # sin(theta) = sin(t / 2).  A row along the bisector meets the first term
+    # (|a . c| = 1, exact 2 cos(t / 2)); a row orthogonal to the bisector in
+    # their plane meets the bound exactly (2 sin(t / 2) both)
+    r, t = 6, 0.3
+    b = np.zeros((2, r))
+    b[0, 0] = 2.0
+    b[1, :2] = 2.0 * np.cos(t), 2.0 * np.sin(t)
+    c, s, bmax = recon.tile_cone(b)
+    assert bmax == 2.0 and abs(s - np.sin(t / 2)) < 1e-12
+    a = np.zeros((2, r))
+    a[0, :2] = np.cos(t / 2), np.sin(t / 2)
+    a[1, :2] = -np.sin(t / 2), np.cos(t / 2)
+    exact = np.max(np.abs(a @ b.T), axis=1)
+    bound = recon.cone_bound(a, c, s, bmax)
+    assert abs(exact[0] - 2.0 * np.cos(t / 2)) < 1e-12 and bound[0] >= exact[0]
+    assert abs(exact[1] - 2.0 * np.sin(t / 2)) < 1e-12 and abs(bound[1] - exact[1]) < 1e-12
+
+
+def test_cone_bound_rules_out_tiles_of_other_directions():
+    # columns clustered around e_0, rows along e_1: the bound is small, while
+    # Cauchy-Schwarz alone (||a|| max ||b||) would keep the tile
+    rng = np.random.default_rng(22)
+    r = 10
+    e0 = np.zeros(r); e0[0] = 1.0
+    b = e0[None, :] + 0.05 * rng.standard_normal((256, r))
+    a = np.zeros((1, r)); a[0, 1] = 1.0
+    c, s, bmax = recon.tile_cone(b)
+    bound = recon.cone_bound(a, c, s, bmax)[0]
+    assert bound < 0.35 * bmax * np.linalg.norm(a)
+    assert np.max(np.abs(a @ b.T)) <= bound
