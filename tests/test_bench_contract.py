@@ -40,3 +40,25 @@ def test_reference_arm_other_ranks_exit_without_work():
     p = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr[-3000:]
     assert p.stdout.strip() == ""
+
+
+def test_roofline_traffic_only_for_the_source_it_was_measured_on(tmp_path, monkeypatch):
+    # the committed per-launch DRAM bytes are reported while the kernel's
+    # source is the one the counters were taken on, and dropped otherwise
+    sys.path.insert(0, ROOT)
+    import bench
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    rec = t["screen_tc_kernel"]
+    assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") == rec["dram_bytes_per_launch"]
+    assert bench.kernel_traffic("k_topk_tc.cu", "no_such_kernel") is None
+    # a copy of the tree whose screen source differs by one byte: no traffic
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(t))
+    csrc = tmp_path / "paper_2407_19892_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = open(os.path.join(ROOT, "paper_2407_19892_gb300", "csrc", "k_topk_tc.cu"), "rb").read()
+    (csrc / "k_topk_tc.cu").write_bytes(src + b" ")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") is None
+    (csrc / "k_topk_tc.cu").write_bytes(src)
+    assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") == rec["dram_bytes_per_launch"]
