@@ -62,3 +62,27 @@ def test_roofline_traffic_only_for_the_source_it_was_measured_on(tmp_path, monke
     assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") is None
     (csrc / "k_topk_tc.cu").write_bytes(src)
     assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") == rec["dram_bytes_per_launch"]
+
+
+def test_clock_samples_give_median_max_and_throttle_reasons(tmp_path):
+    # nvidia-smi's csv rows as the sampler receives them (one malformed line)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    csv = tmp_path / "clocks.csv"
+    csv.write_text("0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+                   "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+                   "garbage line\n"
+                   "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = Done(), str(csv)
+    c = s.stop()
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not csv.exists()
