@@ -130,28 +130,3 @@ def topn_from_row_lists(idx: np.ndarray, val: np.ndarray, n: int):
         return i, j, vals, True
     kth = np.abs(val[:, k - 1])
     return i, j, vals, bool(np.all(kth < abs(vals[-1])))
-
-
-def tile_cone(b: np.ndarray):
-    """A cone holding the columns b_j (rows of ``b``) up to sign: unit centre
-    c (the sign-aligned mean direction), sin of the largest angle between a
-    column's line and c, and the largest column norm.  Not in the paper: a
-    bound for skipping tiles of the threshold-while-recomposing loop."""
-    b = np.asarray(b, dtype=np.float64)
-    nrm = np.linalg.norm(b, axis=1)
-    u = b / np.where(nrm > 0, nrm, 1.0)[:, None]
-    s = np.sign(u @ u[int(np.argmax(nrm))])
-    s[s == 0] = 1.0
-    c = (u * s[:, None]).sum(axis=0)
-    c /= np.linalg.norm(c)
-    cosmin = float(np.min(np.abs(u[nrm > 0] @ c))) if np.any(nrm > 0) else 1.0
-    return c, float(np.sqrt(max(0.0, 1.0 - cosmin * cosmin))), float(nrm.max())
-
-
-def cone_bound(a: np.ndarray, c: np.ndarray, sin_theta: float, bmax: float) -> np.ndarray:
-    """Upper bound of max_j |a_i . b_j| over a tile with cone (c, sin_theta,
-    bmax): writing b_j / ||b_j|| = +-(cos t c + sin t d), d a unit vector
-    orthogonal to c and t <= theta, |a . b_j| <= bmax (|a . c| + sin_theta
-    ||a||).  ``a``: rows a_i."""
-    a = np.asarray(a, dtype=np.float64)
-    return bmax * (np.abs(a @ c) + sin_theta * np.linalg.norm(a, axis=1))

@@ -71,6 +71,67 @@ def test_ties_break_by_lower_column_and_diagonal_excluded():
     assert np.all(gap == 0)
 
 
+def _planted_gap_matrix():
+    """A dense symmetric 16 x 16 matrix whose rows have known, distinct
+    off-diagonal magnitudes (random signs, a dominant diagonal that must
+    never count), with row 0 planted so that its 3rd and 4th magnitudes are
+    1e-5 apart relative to the 3rd, and row 1 so that its 3rd-4th gap
+    differs from its 4th-5th gap and from the gap over the 4th."""
+    rng = np.random.default_rng(31)
+    d = 16
+    psi = np.zeros((d, d))
+    mags = rng.permutation(np.linspace(0.05, 0.95, d * (d - 1) // 2))
+    iu = np.triu_indices(d, 1)
+    psi[iu] = mags * rng.choice([-1.0, 1.0], size=mags.size)
+    # row 0: magnitudes 2.0, 1.5, 1.2, 1.2 (1 - 1e-5), then the rest below 1
+    for j, m in zip((5, 9, 2, 13), (2.0, -1.5, 1.2, -1.2 * (1.0 - 1e-5))):
+        psi[0, j] = m
+    # row 1: 3.0, 2.5, 2.0, 1.6, 1.5: gap(k=3) = 0.2, gap over the 4th 0.25,
+    # gap(4th, 5th) = 0.0625
+    for j, m in zip((7, 3, 12, 15, 6), (3.0, 2.5, -2.0, 1.6, -1.5)):
+        psi[1, j] = m
+    psi = np.triu(psi, 1)
+    psi = psi + psi.T
+    np.fill_diagonal(psi, 50.0 + np.arange(d))
+    return psi
+
+
+def _sorted_gap(row, i, k):
+    """Brute force: the full sorted list of a row's off-diagonal magnitudes."""
+    a = sorted((abs(x) for j, x in enumerate(row) if j != i), reverse=True)
+    return (a[k - 1] - a[k]) / a[k - 1]
+
+
+def test_topk_gap_on_planted_magnitudes():
+    psi = _planted_gap_matrix()
+    lam, v = np.linalg.eigh(psi)
+    k = 3
+    gap = topk_gap(v, lam, k, block=5)
+    # the recomposition is exact to ~1e-14 of the diagonal; gaps to 1e-11
+    for i in range(psi.shape[0]):
+        assert abs(gap[i] - _sorted_gap(psi[i], i, k)) < 1e-11
+    assert abs(gap[0] - 1e-5) < 1e-11
+    assert abs(gap[1] - 0.2) < 1e-11
+    # an off-by-one (4th vs 5th) or the wrong denominator (the 4th) would give
+    assert abs(gap[1] - 0.0625) > 0.1 and abs(gap[1] - 0.25) > 0.04
+    # sampled rows agree with the full computation
+    sub = topk_gap(v, lam, k, rows=[1, 0, 15])
+    np.testing.assert_allclose(sub, gap[[1, 0, 15]], rtol=0, atol=1e-12)
+    # k = d - 1 has no (k+1)-th entry: an infinite gap
+    assert np.all(np.isinf(topk_gap(v, lam, psi.shape[0] - 1)))
+
+
+def test_topk_gap_random_rows_against_full_sort():
+    rng = np.random.default_rng(32)
+    v = rng.standard_normal((70, 9))
+    lam = rng.uniform(-2.0, 3.0, 9)
+    psi = recompose(v, lam)
+    for k in (1, 4, 10):
+        gap = topk_gap(v, lam, k, block=16)
+        ref = np.array([_sorted_gap(psi[i], i, k) for i in range(70)])
+        np.testing.assert_allclose(gap, ref, rtol=1e-9, atol=1e-13)
+
+
 def test_sampled_rows_equal_full_rows():
     rng = np.random.default_rng(15)
     v = rng.standard_normal((50, 4))
@@ -164,57 +225,3 @@ def test_topn_from_row_lists_refuses_a_clique_its_lists_cannot_hold():
     gi, gj, _ = recon.topn_edges(V, lam, 66)
     assert np.array_equal(i, gi) and np.array_equal(j, gj)
     assert np.all(i < 12) and np.all(j < 12)
-
-
-# ---- cone bound for skipping column tiles ---------------------------------------
-
-def test_cone_bound_bounds_every_column_of_the_tile():
-    rng = np.random.default_rng(21)
-    for trial in range(50):
-        r = int(rng.integers(2, 12))
-        centre = rng.standard_normal(r)
-        spread = 10.0 ** rng.uniform(-3, 0.5)
-        b = centre[None, :] + spread * rng.standard_normal((64, r))
-        b *= rng.choice([-1.0, 1.0], size=(64, 1)) * rng.uniform(0.2, 3.0, size=(64, 1))
-        a = rng.standard_normal((40, r)) * rng.uniform(0.1, 10.0, size=(40, 1))
-        c, s, bmax = recon.tile_cone(b)
-        exact = np.max(np.abs(a @ b.T), axis=1)
-        assert np.all(exact <= cone_bound_tol(recon.cone_bound(a, c, s, bmax)))
-
-
-def cone_bound_tol(x):
-    return x * (1.0 + 1e-12) + 1e-300
-
-
-def test_cone_bound_is_attained_for_aligned_and_boundary_columns():
-    # two columns of norm 2 at angle t: the cone's centre is their bisector,
-    # sin(theta) = sin(t / 2).  A row along the bisector meets the first term
-    # (|a . c| = 1, exact 2 cos(t / 2)); a row orthogonal to the bisector in
-    # their plane meets the bound exactly (2 sin(t / 2) both)
-    r, t = 6, 0.3
-    b = np.zeros((2, r))
-    b[0, 0] = 2.0
-    b[1, :2] = 2.0 * np.cos(t), 2.0 * np.sin(t)
-    c, s, bmax = recon.tile_cone(b)
-    assert bmax == 2.0 and abs(s - np.sin(t / 2)) < 1e-12
-    a = np.zeros((2, r))
-    a[0, :2] = np.cos(t / 2), np.sin(t / 2)
-    a[1, :2] = -np.sin(t / 2), np.cos(t / 2)
-    exact = np.max(np.abs(a @ b.T), axis=1)
-    bound = recon.cone_bound(a, c, s, bmax)
-    assert abs(exact[0] - 2.0 * np.cos(t / 2)) < 1e-12 and bound[0] >= exact[0]
-    assert abs(exact[1] - 2.0 * np.sin(t / 2)) < 1e-12 and abs(bound[1] - exact[1]) < 1e-12
-
-
-def test_cone_bound_rules_out_tiles_of_other_directions():
-    # columns clustered around e_0, rows along e_1: the bound is small, while
-    # Cauchy-Schwarz alone (||a|| max ||b||) would keep the tile
-    rng = np.random.default_rng(22)
-    r = 10
-    e0 = np.zeros(r); e0[0] = 1.0
-    b = e0[None, :] + 0.05 * rng.standard_normal((256, r))
-    a = np.zeros((1, r)); a[0, 1] = 1.0
-    c, s, bmax = recon.tile_cone(b)
-    bound = recon.cone_bound(a, c, s, bmax)[0]
-    assert bound < 0.35 * bmax * np.linalg.norm(a)
-    assert np.max(np.abs(a @ b.T)) <= bound
