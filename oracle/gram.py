@@ -70,3 +70,21 @@ def gram_multimodal(tensors, axis_labels, label) -> np.ndarray:
         g = gram(t, labels.index(label))
         s = g if s is None else s + g
     return s
+
+
+def log1p_centred_gram_blocks(chunks):
+    """Column Gram of the centred log1p matrix, for a matrix given as row
+    blocks (too large for FP64 in memory): with Y = log1p(counts) and mu its
+    column means, (Y - 1 mu^T)^T (Y - 1 mu^T) = sum_b Y_b^T Y_b - n mu mu^T
+    (the same rank-one correction as the sparse path).  One pass over the
+    blocks.  Returns (S, mu, n), FP64."""
+    s, tot, n = None, None, 0
+    for c in chunks:
+        y = np.log1p(np.asarray(c, dtype=np.float64))
+        g = y.T @ y
+        cs = y.sum(axis=0)
+        s = g if s is None else s + g
+        tot = cs if tot is None else tot + cs
+        n += y.shape[0]
+    mu = tot / n
+    return s - n * np.outer(mu, mu), mu, n

@@ -35,3 +35,12 @@ def two_axis_spectra(x: np.ndarray, r_rows: int, r_cols: int):
     e_rows = e_all[:r_rows]
     v_rows = dual_lift(x, w_all[:, :r_rows], e_rows)
     return e_rows, v_rows, e_cols, v_cols
+
+
+def dual_lift_blocks(chunks, mu: np.ndarray, w_r: np.ndarray, e_r: np.ndarray) -> np.ndarray:
+    """``dual_lift`` of the centred log1p matrix given as row blocks of
+    counts: each block is log1p-transformed, centred by the column means mu
+    and multiplied by W_r diag(E_r)^-1/2; the blocks' rows are stacked."""
+    wd = np.asarray(w_r, dtype=np.float64) / np.sqrt(np.asarray(e_r, dtype=np.float64))[None, :]
+    out = [(np.log1p(np.asarray(c, dtype=np.float64)) - mu[None, :]) @ wd for c in chunks]
+    return np.concatenate(out, axis=0)

@@ -103,3 +103,28 @@ def test_dual_lift_gives_left_singular_vectors():
     np.testing.assert_allclose(u5.T @ u5, np.eye(5), atol=1e-12)
     ev_rows = np.sort(np.linalg.eigvalsh(srow))[::-1][:5]
     np.testing.assert_allclose(e5, ev_rows, rtol=1e-10)
+
+
+@pytest.mark.parametrize("block", [1, 7, 64, 1000])
+def test_centred_gram_and_lift_over_row_blocks(block):
+    # The row-blocked forms used at a million cells equal the plain
+    # definitions: the Gram of log1p_centre(counts) and the dual lift of it,
+    # whatever the blocking (a dropped rank-one term or a mean over the wrong
+    # count would change every entry)
+    from oracle.gram import log1p_centred_gram_blocks
+    from oracle.spectra import dual_lift_blocks
+    rng = np.random.default_rng(41)
+    c = rng.poisson(rng.gamma(0.5, 2.0, size=(1, 9)), size=(120, 9)).astype(np.float32)
+    c[:, 4] = 3.0  # a constant column: centred to exactly zero
+    x = log1p_centre(c)
+    ref = gram(x, 1)
+    chunks = lambda: (c[i:i + block] for i in range(0, c.shape[0], block))
+    s, mu, n = log1p_centred_gram_blocks(chunks())
+    assert n == 120
+    np.testing.assert_allclose(mu, np.log1p(c.astype(np.float64)).mean(axis=0), rtol=1e-14)
+    np.testing.assert_allclose(s, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert np.all(np.abs(s[4]) <= 1e-12 * np.abs(ref).max())
+    e, w = top_eigh(ref, 3)
+    u = dual_lift_blocks(chunks(), mu, w, e)
+    np.testing.assert_allclose(u, dual_lift(x, w, e), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(u.T @ u, np.eye(3), atol=1e-10)
