@@ -68,6 +68,9 @@ typedef enum {
 #define GMGM_DEV_INFEASIBLE 0x4
 #define GMGM_DEV_CAND_OVERFLOW 0x8
 #define GMGM_DEV_TIMEOUT 0x10
+#define GMGM_DEV_NOT_COUNTS 0x20  /* gmgm_skeptic met a value that is not a
+                                     count (negative, fractional, > 2^24,
+                                     NaN or Inf) */
 
 typedef enum {
   GMGM_FP32 = 0,   /* FP32 SIMT arithmetic (the plain comparator form) */
@@ -137,6 +140,47 @@ int gmgm_preprocess(gmgm_handle* h, int64_t n, int64_t p,
                     uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t,
                     double* colmean_out);
 
+/* ---- rank-based statistics (Nonparanormal Skeptic, COCA form) ---------- */
+
+#define GMGM_AXIS_ROWS 0  /* rank each row across its p entries (cells x genes:
+                             the cell axis, each cell over its genes) */
+#define GMGM_AXIS_COLS 1  /* rank each column across the n rows (the gene
+                             axis, each gene over the cells) */
+
+/* Normal scores of the ranks of a count matrix along one axis (Section "The
+ * model": the Gaussian-copula assumption and the Nonparanormal Skeptic;
+ * Section "Algorithm": the COCA form, ranks mapped to a normal distribution
+ * before the Gram; the worked example of the appendix "Preserving input
+ * sparsity" fixes the conventions).  Along GMGM_AXIS_ROWS each row of the
+ * n x p matrix is ranked across its p entries; along GMGM_AXIS_COLS each
+ * column across its n entries.  The rank of an entry is 1 + the number of
+ * strictly smaller entries of its row (column), so ties take the lowest
+ * rank of their group; rank k of N entries maps to the score
+ * Phi^-1(k / (N + 1)), evaluated in FP64 and rounded to FP32.  The axis'
+ * Gram is then the Gram of the scores (S_genes = Z^T Z for the column
+ * scores Z; the cell axis through the dual Gram of the row scores), with
+ * no re-centring.
+ *   counts     device, n x p FP32, leading dimension ldc >= p: counts, i.e.
+ *              non-negative integers <= 2^24 (ranks come from counting, not
+ *              sorting).  Any other value sets GMGM_DEV_NOT_COUNTS in the
+ *              device status word and leaves the outputs undefined.
+ *   z_out      device, optional, n x p FP32 scores (ldz >= p); required with
+ *              the planes along GMGM_AXIS_ROWS (they are written from it).
+ *   zt_hi, zt_lo  device, optional (both or neither): the BF16 split of
+ *              Z^T, p x ld_t (ld_t >= n, a multiple of 64; columns n..ld_t-1
+ *              zero), the layout gmgm_gram and gmgm_lift read.
+ *   ranks_out  device, optional, n x p int32 ranks (ldr >= p).
+ * Work: GMGM_AXIS_COLS reads the counts three times (per-column maxima, read
+ * back to size one histogram per column; histograms; scores) and
+ * synchronises the stream once; GMGM_AXIS_ROWS reads them once (one warp
+ * per row, a shared-memory histogram of the values below 1024; a larger
+ * value is ranked by counting the larger entries of its row).
+ * Errors: GMGM_E_ARG (shapes, strides, no output, missing z_out),
+ * GMGM_E_NOMEM; device bit GMGM_DEV_NOT_COUNTS. */
+int gmgm_skeptic(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, int axis,
+                 float* z_out, int64_t ldz, uint16_t* zt_hi, uint16_t* zt_lo, int64_t ld_t,
+                 int32_t* ranks_out, int64_t ldr);
+
 /* ---- step 1: Gram ------------------------------------------------------- */
 
 /* A batch of equally shaped matrices X_b (rows x cols), b < batch. */
@@ -194,12 +238,20 @@ int gmgm_spectra(gmgm_handle* h, int64_t d, const double* S, int64_t lds,
 
 /* Dual lift (Section "Algorithm": eigenvectors of S_l are singular vectors
  * of mat_l[D]; Algorithm 1 takes the top-r left singular vectors): for the
- * matrix X (rows x cols, FP32 m->x) and the top-r eigenpairs (W, E) of
- * X^T X, U = X W diag(E)^-1/2 are the top-r eigenvectors of X X^T.
+ * matrix X (rows x cols) and the top-r eigenpairs (W, E) of X^T X,
+ * U = X W diag(E)^-1/2 are the top-r eigenvectors of X X^T.
+ *   m      one matrix (batch 1).  With its BF16 split of X^T (m->xt_hi and
+ *          m->xt_lo, cols x ld_t, as gmgm_preprocess writes it) and r <= 64
+ *          the product runs on the tensor cores from the two planes
+ *          (3xBF16 products, the FP32 accumulation drained every 128
+ *          columns of X; error about 1e-6 of max |U|); otherwise from the
+ *          FP32 matrix m->x on the FP32 pipe.
  *   W      device, cols x r FP64 row-major, leading dimension ldw.
  *   E      device, r FP64, all > 0.
  *   U      device, rows x r FP32 row-major, leading dimension ldu >= r.
- * Errors: GMGM_E_ARG (batch != 1, shapes). */
+ * 1 <= r <= 256.  Errors: GMGM_E_ARG (batch != 1, shapes, only one of the
+ * planes given, ld_t < rows or not a multiple of 64, no FP32 matrix where
+ * the tensor-core form does not apply). */
 int gmgm_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r,
               const double* W, int64_t ldw, const double* E,
               float* U, int64_t ldu);

@@ -21,6 +21,8 @@ STATUS = {0: "GMGM_OK", -1: "GMGM_E_ARG", -2: "GMGM_E_CUDA", -3: "GMGM_E_NOMEM",
           -7: "GMGM_E_CAND_OVERFLOW", -8: "GMGM_E_TIMEOUT"}
 FP32, BF16, BF16X3, FP64 = 0, 1, 2, 3
 SIDE_COLS, SIDE_ROWS = 0, 1
+AXIS_ROWS, AXIS_COLS = 0, 1
+DEV_NOT_COUNTS = 0x20
 MAX_AXES, MAX_MODALITIES = 4, 4
 
 
@@ -81,6 +83,8 @@ SIGNATURES = {
     "gmgm_kernel_launches": (ctypes.c_uint64, []),
     "gmgm_preprocess": (c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp,
                                 c_i64, c_vp]),
+    "gmgm_skeptic": (c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp, c_vp, c_i64,
+                             c_vp, c_i64]),
     "gmgm_gram": (c_int, [c_vp, ctypes.POINTER(Matrix), c_int, c_int, c_vp, c_i64, c_int]),
     "gmgm_spectra": (c_int, [c_vp, c_i64, c_vp, c_i64, c_i32, c_vp, c_i32, c_vp, c_i64]),
     "gmgm_lift": (c_int, [c_vp, ctypes.POINTER(Matrix), c_i32, c_vp, c_i64, c_vp, c_vp, c_i64]),

@@ -114,6 +114,33 @@ def preprocess(counts: torch.Tensor, split: bool = True, inplace: bool = False, 
     return x, hi, lo, ld_t
 
 
+# ---- rank-based statistics (Nonparanormal Skeptic, COCA form) ----------------
+
+def skeptic(counts: torch.Tensor, axis: int, z: bool = True, planes: bool = True, ranks: bool = False,
+            h: Handle = None):
+    """Normal scores Phi^-1(rank / (N + 1)) of the ranks of a count matrix
+    (n x p FP32 on the GPU) along ``axis`` (AXIS_ROWS: each row over its p
+    entries; AXIS_COLS: each column over its n entries), ties at the lowest
+    rank.  Returns (Z n x p FP32 or None, zt_hi, zt_lo (p x ld_t BF16 split
+    of Z^T) or None, ld_t, ranks n x p int32 or None)."""
+    h = h or handle(counts.device)
+    _need_cuda(counts, torch.float32, "counts")
+    if counts.dim() != 2 or counts.stride(1) != 1:
+        raise ValueError("counts must be a row-major 2-D tensor")
+    n, p = counts.shape
+    dev = counts.device
+    if axis == L.AXIS_ROWS and planes:
+        z = True
+    zt = torch.empty(n, p, dtype=torch.float32, device=dev) if z else None
+    ld_t = ((n + 63) // 64) * 64 if planes else 0
+    hi = torch.empty(p, ld_t, dtype=torch.bfloat16, device=dev) if planes else None
+    lo = torch.empty(p, ld_t, dtype=torch.bfloat16, device=dev) if planes else None
+    rk = torch.empty(n, p, dtype=torch.int32, device=dev) if ranks else None
+    h.check(h.lib.gmgm_skeptic(h.h, n, p, _ptr(counts), counts.stride(0), axis, _ptr(zt), p, _ptr(hi), _ptr(lo),
+                               ld_t, _ptr(rk), p))
+    return zt, hi, lo, ld_t, rk
+
+
 # ---- Gram ------------------------------------------------------------------
 
 def _matrix(x=None, xt_hi=None, xt_lo=None, ld_t=0, rows=None, cols=None, batch=1, batch_stride=0):
@@ -172,13 +199,16 @@ def spectra(S: torch.Tensor, r: int, vectors: bool = True, rv: int = None, h: Ha
     return ev, W
 
 
-def lift(x: torch.Tensor, W: torch.Tensor, E: torch.Tensor, r: int, h: Handle = None):
-    """U = X W_r diag(E_r)^-1/2 (rows x r, FP32)."""
+def lift(x: torch.Tensor, W: torch.Tensor, E: torch.Tensor, r: int, xt_hi=None, xt_lo=None, ld_t: int = 0,
+         h: Handle = None):
+    """U = X W_r diag(E_r)^-1/2 (rows x r, FP32).  With the BF16 planes of
+    X^T (xt_hi, xt_lo, ld_t) and r <= 64 it runs on the tensor cores from
+    them (3xBF16); otherwise from X in FP32."""
     h = h or handle(x.device)
     _need_cuda(x, torch.float32, "x")
     W = W.contiguous()
     E = E.contiguous()
-    m = _matrix(x)
+    m = _matrix(x, xt_hi, xt_lo, ld_t)
     U = torch.empty(x.shape[0], r, dtype=torch.float32, device=x.device)
     h.check(h.lib.gmgm_lift(h.h, ctypes.byref(m), r, _ptr(W), W.stride(0), _ptr(E), _ptr(U), r))
     return U
@@ -307,7 +337,7 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
         h.check(h.lib.gmgm_warmstart_infer(h.h, _ptr(warm_params), _ptr(e_rows), r_rows, _ptr(e_cols), r_cols,
                                            0.0, _ptr(i0), _ptr(i1)))
         init = [i0, i1]
-    v_rows = lift(x, W[:, :r_rows].contiguous(), e_rows, r_rows, h=h)
+    v_rows = lift(x, W[:, :r_rows].contiguous(), e_rows, r_rows, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, h=h)
     (lam_rows, lam_cols), st = eigsolve([e_rows, e_cols], [(0, 1)], tol=tol, fp32_phase=fp32_phase,
                                         init=init, h=h)
     ir, vr, sr = topk_network(v_rows, lam_rows, k_rows, topk_prec, h=h)
@@ -368,7 +398,7 @@ def fit_multimodal(counts, r_cells: int, ks, gram_prec: int = L.BF16X3, topk_pre
         off += p
     S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
     e_c, W_c = spectra(S, r_cells, True, h=h)
-    E, V, Ss = [e_c], [lift(x, W_c, e_c, r_cells, h=h)], [S]
+    E, V, Ss = [e_c], [lift(x, W_c, e_c, r_cells, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)], [S]
     off = 0
     for p in ps:
         Sb = S[off:off + p, off:off + p]

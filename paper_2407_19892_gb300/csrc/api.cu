@@ -165,6 +165,30 @@ int gmgm_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float* counts, i
   return GMGM_OK;
 }
 
+int gmgm_skeptic(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, int axis, float* z_out,
+                 int64_t ldz, uint16_t* zt_hi, uint16_t* zt_lo, int64_t ld_t, int32_t* ranks_out, int64_t ldr) {
+  if (!h) return GMGM_E_ARG;
+  if (n < 1 || p < 1 || n > (int64_t(1) << 31) - 2 || p > (int64_t(1) << 31) - 2 || !counts || ldc < p)
+    return fail(h, GMGM_E_ARG, "gmgm_skeptic: need 1 <= n, p < 2^31, ldc >= p, non-null counts");
+  if (axis != GMGM_AXIS_ROWS && axis != GMGM_AXIS_COLS)
+    return fail(h, GMGM_E_ARG, "gmgm_skeptic: axis must be GMGM_AXIS_ROWS or GMGM_AXIS_COLS");
+  if (!z_out && !zt_hi && !ranks_out) return fail(h, GMGM_E_ARG, "gmgm_skeptic: no output requested");
+  if ((z_out && ldz < p) || (ranks_out && ldr < p))
+    return fail(h, GMGM_E_ARG, "gmgm_skeptic: ldz, ldr must be >= p");
+  if ((zt_hi == nullptr) != (zt_lo == nullptr))
+    return fail(h, GMGM_E_ARG, "gmgm_skeptic: zt_hi and zt_lo must both be set or both NULL");
+  if (zt_hi && (ld_t < n || ld_t % 64 != 0 || ((uintptr_t)zt_hi % 16) || ((uintptr_t)zt_lo % 16)))
+    return fail(h, GMGM_E_ARG, "gmgm_skeptic: ld_t must be >= n, a multiple of 64, 16-byte aligned planes");
+  if (axis == GMGM_AXIS_ROWS && zt_hi && !z_out)
+    return fail(h, GMGM_E_ARG, "gmgm_skeptic: GMGM_AXIS_ROWS writes the planes from z_out; pass z_out");
+  if ((const void*)z_out == (const void*)counts)
+    return fail(h, GMGM_E_ARG, "gmgm_skeptic: z_out must not alias counts");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  if (axis == GMGM_AXIS_ROWS)
+    return gmgm::skeptic_rows(h, n, p, counts, ldc, z_out, ldz, zt_hi, zt_lo, ld_t, ranks_out, ldr);
+  return gmgm::skeptic_cols(h, n, p, counts, ldc, z_out, ldz, zt_hi, zt_lo, ld_t, ranks_out, ldr);
+}
+
 int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec, double* S,
               int64_t lds, int accumulate) {
   if (!h) return GMGM_E_ARG;
@@ -220,11 +244,23 @@ int gmgm_spectra(gmgm_handle* h, int64_t d, const double* S, int64_t lds, int32_
 int gmgm_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const double* W, int64_t ldw,
               const double* E, float* U, int64_t ldu) {
   if (!h) return GMGM_E_ARG;
-  if (!m || !m->x || m->batch != 1 || m->rows < 1 || m->cols < 1 || m->ld < m->cols)
-    return fail(h, GMGM_E_ARG, "gmgm_lift: need one FP32 matrix");
+  if (!m || m->batch != 1 || m->rows < 1 || m->cols < 1)
+    return fail(h, GMGM_E_ARG, "gmgm_lift: need one matrix");
   if (r < 1 || r > 256 || r > m->cols || !W || !E || !U || ldw < r || ldu < r)
     return fail(h, GMGM_E_ARG, "gmgm_lift: need 1 <= r <= min(256, cols), ldw, ldu >= r");
+  if ((m->xt_hi != nullptr) != (m->xt_lo != nullptr))
+    return fail(h, GMGM_E_ARG, "gmgm_lift: xt_hi and xt_lo must both be set or both be NULL");
+  if (m->xt_hi && (m->ld_t < m->rows || m->ld_t % 64 != 0))
+    return fail(h, GMGM_E_ARG, "gmgm_lift: need ld_t >= rows, ld_t % 64 == 0 with the BF16 planes");
   GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  if (gmgm::lift_tc_eligible(m, r)) {
+    int rc = gmgm::ensure_scratch(h, gmgm::lift_tc_scratch_bytes(m));
+    if (rc) return rc;
+    GMGM_CUDA_TRY(h, gmgm::launch_lift_tc(h, m, r, W, ldw, E, U, ldu, h->scratch));
+    return GMGM_OK;
+  }
+  if (!m->x || m->ld < m->cols)
+    return fail(h, GMGM_E_ARG, "gmgm_lift: need the FP32 matrix (or its BF16 planes with r <= 64)");
   int rc = gmgm::ensure_scratch(h, size_t(m->cols) * ((r + 63) / 64) * 64 * sizeof(float) + 256);
   if (rc) return rc;
   GMGM_CUDA_TRY(h, gmgm::launch_lift(h, m, r, W, ldw, E, U, ldu, static_cast<float*>(h->scratch)));

@@ -83,6 +83,17 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d, const double* S, int64_t lds, 
 
 cudaError_t launch_lift(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const double* W,
                         int64_t ldw, const double* E, float* U, int64_t ldu, float* wscr);
+// tensor-core lift from the BF16 planes of X^T (r <= 64)
+bool lift_tc_eligible(const gmgm_matrix* m, int32_t r);
+size_t lift_tc_scratch_bytes(const gmgm_matrix* m);
+cudaError_t launch_lift_tc(gmgm_handle* h, const gmgm_matrix* m, int32_t r, const double* W, int64_t ldw,
+                           const double* E, float* U, int64_t ldu, void* scratch);
+
+// rank-based scores (Nonparanormal Skeptic / COCA) of a count matrix
+int skeptic_rows(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, float* z, int64_t ldz,
+                 uint16_t* hi, uint16_t* lo, int64_t ld_t, int32_t* ranks, int64_t ldr);
+int skeptic_cols(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, float* z, int64_t ldz,
+                 uint16_t* hi, uint16_t* lo, int64_t ld_t, int32_t* ranks, int64_t ldr);
 
 struct SolveDesc;  // defined in k_solve.cu
 size_t solve_scratch_bytes(const gmgm_problem* p);

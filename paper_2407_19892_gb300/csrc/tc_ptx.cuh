@@ -140,6 +140,20 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor, MN-major operand in the 128-byte swizzled
+// canonical layout: each K row holds 64 consecutive M (or N) elements in 128
+// bytes, 8 K rows form a 1024-byte swizzle atom; `sbo` bytes between 8-row K
+// groups, `lbo` bytes between 64-element M groups.  Tile base 1024-aligned.
+__device__ __forceinline__ uint64_t sdesc_mn128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);        // start address
+  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;     // leading byte offset: M groups
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;     // stride byte offset: K groups
+  d |= uint64_t(1) << 46;                        // descriptor version (sm_100 family)
+  d |= uint64_t(2) << 61;                        // layout: 128-byte swizzle
+  return d;
+}
+
 // Instruction descriptor for kind::f16: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4)                       // D format: FP32
@@ -147,6 +161,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | (1u << 10)                    // B format: BF16
          | (uint32_t(N >> 3) << 17)      // N / 8
          | (uint32_t(M >> 4) << 24);     // M / 16
+}
+
+// The same with A MN-major (transposed A: bit 15), B K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_amn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 15);
 }
 
 }  // namespace tc

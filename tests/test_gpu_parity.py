@@ -176,6 +176,23 @@ def test_lift_matches_oracle(g, cuda_dev):
     assert np.max(np.abs(U - ref)) <= 1e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("n,p,r", [(1000, 300, 50), (70001, 2000, 64), (257, 61, 7), (5000, 130, 33)])
+def test_lift_tensor_core_from_planes(g, cuda_dev, n, p, r):
+    # the 3xBF16 tensor-core lift from the BF16 planes of X^T (several
+    # 256-cell blocks and 128-gene drains, ragged cells and genes) against the
+    # oracle's FP64 lift of the same centred log1p matrix, and the FP32 form
+    counts = scrna_counts(n, p, 8, seed=300 + n + r)
+    x, hi, lo, ld_t = g.preprocess(counts.to(cuda_dev), split=True)
+    x64 = og.log1p_centre(counts.numpy())
+    e, w = osp.top_eigh(og.gram(x64, 1), r)
+    W, E = torch.from_numpy(w).to(cuda_dev), torch.from_numpy(e).to(cuda_dev)
+    U = g.lift(x, W, E, r, xt_hi=hi, xt_lo=lo, ld_t=ld_t).cpu().numpy()
+    ref = osp.dual_lift(x64, w, e)
+    assert np.max(np.abs(U - ref)) <= 1e-5 * np.abs(ref).max()
+    U32 = g.lift(x, W, E, r).cpu().numpy()
+    assert np.max(np.abs(U - U32)) <= 1e-5 * np.abs(ref).max()
+
+
 # ---- eigenvalue solve ------------------------------------------------------------
 
 def _sums(lams, mods):
@@ -538,3 +555,24 @@ def test_spectra_vectors_for_the_top_rv_only(g, cuda_dev):
     ev0, W0 = g.spectra(torch.from_numpy(S).to(cuda_dev), 300, vectors=False)
     assert W0 is None
     np.testing.assert_array_equal(ev0.cpu().numpy(), ev_all.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16"])
+def test_topk_network_gram_2000_genes_every_eigenvalue_free(g, cuda_dev, prec):
+    # The gene network of the 1M-cell workload's shape (d = 2000, k = 20)
+    # with every psi distinct, so all 1999 eigenvectors above the minimum are
+    # formed (tridiagonalisation, bisection, inverse iteration and the
+    # back-transformation at full size) and the screen runs over r = 1999:
+    # every row against the oracle's top-k of the FP64 eigenvectors of S
+    d, k = 2000, 20
+    rng = _rng(91)
+    A = rng.standard_normal((5000, d)) * np.exp(rng.uniform(-2.0, 1.0, d))[None, :]
+    S = A.T @ A
+    w, W = np.linalg.eigh(S)
+    w, W = w[::-1], W[:, ::-1]
+    psi = 1.0 / w + rng.uniform(0.0, 1e-3, d) / w[0]
+    idx, val, st = g.topk_network_gram(torch.from_numpy(S).to(cuda_dev), torch.from_numpy(psi).to(cuda_dev), k,
+                                       getattr(g, prec))
+    frac = _check_topk(W, psi, k, idx.cpu().numpy(), val.cpu().numpy())
+    assert frac > 0.9
+    assert st["screen_err_ratio"] <= 1.0
