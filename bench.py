@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cells", type=int, default=50_000)
     ap.add_argument("--cpu-sample-rows", type=int, default=1000)
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="print the FP64 FMA and special-function throughput of this GPU and exit")
+    ap.add_argument("--workload", default="two_axis",
+                    choices=["two_axis", "multimodal", "tensor3", "skeptic", "sparse"],
+                    help="two_axis: the headline fit; the others print their own line (see other_workload)")
     return ap.parse_args()
 
 
@@ -238,8 +243,166 @@ def reference_arm(a, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def other_workload(a):
+    """The other workloads of the method, one JSON line each (1 GPU):
+      multimodal  500,000 cells x (2,000 genes log1p NB counts + 5,000 peaks
+                  Bernoulli accessibility) sharing the cell axis, cell rank 50,
+                  k = 10 per axis (fit_multimodal);
+      tensor3     one 50 x 400 x 300 FP32 Gaussian tensor from a planted
+                  3-way Kronecker-sum precision, full ranks, k = 10 per axis
+                  (fit_tensor);
+      skeptic     the headline two-axis workload with the rank-based
+                  statistics (Nonparanormal Skeptic / COCA) instead of log1p
+                  + centring: per-gene and per-cell normal scores, each axis'
+                  Gram from its own scores, the cell vectors lifted from the
+                  per-cell scores;
+      sparse      the headline workload from CSR counts (the sparse
+                  preprocessing into the BF16 planes; no dense counts or X).
+    Each step is the whole fit with its inputs resident; stage times in
+    `detail`."""
+    import numpy as np
+    import torch
+    import paper_2407_19892_gb300 as g
+    from paper_2407_19892_gb300 import build, replicas
+    from synth import atac_binary, er_precision, ks_normal_tensor, scrna_counts
+    build.build()
+    lib = g.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = g.handle(dev)
+    stream = torch.cuda.current_stream(dev)
+    detail = {}
+    if a.workload == "multimodal":
+        n, pg, pp, r, cl = 500_000, 2000, 5000, 50, 50
+        c1, lab, _ = scrna_counts(n, pg, cl, seed=a.seed, device=dev, return_clusters=True)
+        c2 = atac_binary(lab, cl, pp, seed=a.seed + 1)
+        s2 = c2.sum(0)
+        c2 = c2[:, (s2 > 0) & (s2 < n)].contiguous()
+        units, unit_name = n, "cells/s"
+        name = (f"multi-modal fit, {n} cells x ({pg} genes log1p NB counts + {c2.shape[1]} peaks Bernoulli "
+                f"accessibility) sharing the cell axis, r_cells={r}, k=10 per axis")
+        metric = "multi-modal fit cells/sec at 500k cells x (2k genes + 5k peaks)"
+
+        def step():
+            return g.fit_multimodal([c1, c2], r, [10, 10, 10], h=h)
+    elif a.workload == "tensor3":
+        rng = np.random.default_rng(a.seed)
+        psis = [er_precision(d, 4.0, rng) for d in (50, 400, 300)]
+        t = torch.from_numpy(ks_normal_tensor(psis, rng).astype(np.float32)).to(dev)
+        units, unit_name = 1, "fits/s"
+        name = "3-axis fit, one 50 x 400 x 300 FP32 tensor (planted 3-way Kronecker-sum precision), full ranks, k=10"
+        metric = "3-axis fit fits/sec at 50 x 400 x 300"
+
+        def step():
+            return g.fit_tensor(t, [10, 10, 10], h=h)
+    else:
+        n, p = a.cells, a.genes
+        counts = scrna_counts(n, p, a.clusters, seed=a.seed, device=dev)
+        units, unit_name = n, "cells/s"
+        if a.workload == "skeptic":
+            name = (f"two-axis fit on rank-based statistics (Nonparanormal Skeptic / COCA), {n} cells x {p} genes "
+                    f"(scRNA-like NB counts, {a.clusters} clusters), r_cells={a.r_cells}, k_cells={a.k_cells}, "
+                    f"k_genes={a.k_genes}")
+            metric = "Skeptic two-axis fit cells/sec at 1M cells x 2k genes"
+
+            def step():
+                return g.fit_two_axis_skeptic(counts, a.r_cells, a.k_cells, a.k_genes, h=h)
+        else:
+            import scipy.sparse as sp
+            c = sp.csr_matrix(counts.cpu().numpy())
+            c.sort_indices()
+            ip = torch.from_numpy(c.indptr.astype(np.int64)).to(dev)
+            ix = torch.from_numpy(c.indices.astype(np.int32)).to(dev)
+            dv = torch.from_numpy(c.data.astype(np.float32)).to(dev)
+            detail["density"] = c.nnz / (n * p)
+            del counts, c
+            name = (f"two-axis fit from CSR counts, {n} cells x {p} genes (scRNA-like NB counts, {a.clusters} "
+                    f"clusters), r_cells={a.r_cells}, full gene spectrum, k_cells={a.k_cells}, k_genes={a.k_genes}")
+            metric = "sparse-input two-axis fit cells/sec at 1M cells x 2k genes"
+            from paper_2407_19892_gb300 import warmstart
+            warm = warmstart.load(dev)
+
+            def step():
+                hi, lo, ld_t, _ = g.preprocess_csr(ip, ix, dv, n, p, h=h)
+                return g.fit_two_axis(None, a.r_cells, p, a.k_cells, a.k_genes, gram_prec=g.BF16X3,
+                                      topk_prec=g.BF16, xt_hi=hi, xt_lo=lo, ld_t=ld_t, rows=n, tol=a.tol,
+                                      warm_params=warm, h=h)
+    torch.cuda.synchronize()
+    for _ in range(a.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = lib.gmgm_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        res = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    launches = (lib.gmgm_kernel_launches() - launches0) // a.steps
+    pk, pk_kind = peaks()
+    roof = None
+    st = res.topk_stats[0] if hasattr(res, "topk_stats") else res.topk_rows_stats
+    if a.workload != "tensor3" and st and st.get("screen_ms", 0) > 0:
+        flops = 2.0 * units * units * (50 if a.workload == "multimodal" else a.r_cells)
+        ach = flops / (st["screen_ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": "screen_tc_kernel", "achieved": ach, "peak": pk["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"],
+                "peak_source": f"{pk_kind} bf16 sustained", "traffic": None}
+        detail["screen_ms"] = st["screen_ms"]
+    if a.workload == "tensor3":
+        sv = res.solve
+        terms = 50 * 400 * 300
+        detail["solve"] = sv
+        detail["grid_terms_per_pass"] = terms
+    else:
+        detail["solve"] = res.solve
+    line = {"metric": metric, "value": units / (ms / 1e3), "unit": unit_name, "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if a.workload != "tensor3" else "f32", "data": "synthetic",
+            "config": {"workload": name, "l2": "inputs resident; larger than L2" if a.workload != "tensor3"
+                       else "inputs resident (24 MB, within L2)"},
+            "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clocks,
+            "detail": detail}
+    print(json.dumps(line), flush=True)
+
+
+def probe_peaks():
+    """FP64 FMA and special-function throughput of this GPU (the library's
+    probes), one JSON line."""
+    import ctypes
+    import torch
+    import paper_2407_19892_gb300 as g
+    from paper_2407_19892_gb300 import build
+    build.build()
+    lib = g.load()
+    h = g.handle(torch.device("cuda", 0))
+    out = {}
+    for name, kind, iters in (("fp64_tflops", 0, 1 << 14), ("sfu_gops", 1, 1 << 14)):
+        best = 0.0
+        for _ in range(3):
+            r = ctypes.c_double(0.0)
+            h.check(lib.gmgm_peak_probe(h.h, kind, iters, ctypes.byref(r)))
+            best = max(best, r.value)
+        out[name] = best / (1e12 if kind == 0 else 1e9)
+    print(json.dumps({"probe": "peaks", **out}), flush=True)
+
+
 def main():
     a = parse()
+    if a.probe_peaks:
+        probe_peaks()
+        return
+    if a.workload != "two_axis":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the headline workload"}))
+            return
+        other_workload(a)
+        return
     from paper_2407_19892_gb300 import replicas
     world, rank, local = replicas.rank_env()
     if a.impl == "reference":
@@ -285,7 +448,8 @@ def main():
         ev[2].record(stream)
         e_all, W = g.spectra(S, a.genes, rv=a.r_cells, h=h)
         ev[3].record(stream)
-        U = g.lift(x, W[:, :a.r_cells].contiguous(), e_all[:a.r_cells].contiguous(), a.r_cells, h=h)
+        U = g.lift(x, W[:, :a.r_cells].contiguous(), e_all[:a.r_cells].contiguous(), a.r_cells, xt_hi=hi,
+                   xt_lo=lo, ld_t=ld_t, h=h)
         ev[4].record(stream)
         e_c = e_all[:a.r_cells].contiguous()
         init = list(warmstart.infer(warm, e_c, e_all, h=h)) if warm is not None else None

@@ -70,7 +70,10 @@ typedef enum {
 #define GMGM_DEV_TIMEOUT 0x10
 #define GMGM_DEV_NOT_COUNTS 0x20  /* gmgm_skeptic met a value that is not a
                                      count (negative, fractional, > 2^24,
-                                     NaN or Inf) */
+                                     NaN or Inf); gmgm_preprocess_csr an entry
+                                     that is negative or non-finite, or a
+                                     column index out of range or out of
+                                     order */
 
 typedef enum {
   GMGM_FP32 = 0,   /* FP32 SIMT arithmetic (the plain comparator form) */
@@ -112,6 +115,17 @@ int gmgm_device_status(gmgm_handle* h);
  * containing "alloc", every call whose scratch has to grow returns
  * GMGM_E_NOMEM instead of allocating (nothing is faulted on the device). */
 int gmgm_probe_wait(gmgm_handle* h, int64_t spins);
+
+/* Throughput probes for roofline denominators no library measures here
+ * (not part of the paper): GMGM_PROBE_FP64 runs independent FP64 FMA chains
+ * on every SM and returns FP64 flop/s; GMGM_PROBE_SFU runs chains of one
+ * approximate reciprocal and one approximate base-2 logarithm per step (the
+ * special-function work of one grid term of the eigenvalue solve) and
+ * returns special-function operations/s.  `iters` steps per chain
+ * (1..2^24); synchronises the stream.  Errors: GMGM_E_ARG. */
+#define GMGM_PROBE_FP64 0
+#define GMGM_PROBE_SFU 1
+int gmgm_peak_probe(gmgm_handle* h, int kind, int64_t iters, double* rate);
 
 /* Library version string, e.g. "gmgm 0.1 sm_103a". */
 const char* gmgm_version(void);
@@ -180,6 +194,45 @@ int gmgm_preprocess(gmgm_handle* h, int64_t n, int64_t p,
 int gmgm_skeptic(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, int axis,
                  float* z_out, int64_t ldz, uint16_t* zt_hi, uint16_t* zt_lo, int64_t ld_t,
                  int32_t* ranks_out, int64_t ldr);
+
+/* The preprocessing of a sparse count matrix without its dense form (the
+ * appendix "Preserving input sparsity": a transformed matrix with the
+ * input's sparsity plus a rank-one term).  log1p keeps zeros at zero and the
+ * centring subtracts the rank-one 1 mu^T, so X = log1p(C) - 1 mu^T: the
+ * column means mu come from the non-zeros, and the BF16 hi/lo planes of X^T
+ * are written tile by tile (each tile starts at -mu, the rank-one term, and
+ * the rows' non-zeros are scattered over it).  The dense counts and the
+ * dense FP32 X are never formed; gmgm_gram (BF16 / BF16X3) and gmgm_lift
+ * read the planes.
+ *   indptr   device, n + 1 int64 row offsets; indices device, int32 column
+ *            indices, strictly ascending within a row; data device, FP32
+ *            counts (finite, >= 0).  An entry breaking these is left out
+ *            and sets GMGM_DEV_NOT_COUNTS.
+ *   xt_hi, xt_lo  device, p x ld_t BF16 (ld_t >= n, a multiple of 64;
+ *            cells n..ld_t-1 written as zero).
+ *   colmean_out  device, optional, p FP64 column means of log1p(C).
+ * 1 <= p <= 16384.  Errors: GMGM_E_ARG. */
+int gmgm_preprocess_csr(gmgm_handle* h, int64_t n, int64_t p, const int64_t* indptr, const int32_t* indices,
+                        const float* data, uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t, double* colmean_out);
+
+/* The preprocessing of a matrix whose rows (cells) are split over several
+ * calls or processes (the cell-sharded fit: S_genes = X^T X is a sum over
+ * row blocks, Section "Algorithm"), in two steps with an exchange between:
+ *   gmgm_colsum_log1p   FP64 column sums of log1p(counts) over this row
+ *                       block (n x p, device), written to (accumulate = 0)
+ *                       or added to (accumulate = 1) colsum (device, p);
+ *   gmgm_centre         X = log1p(counts) - colsum / n_total for this row
+ *                       block, with the optional BF16 split of X^T exactly
+ *                       as gmgm_preprocess (ld_t >= n, a multiple of 64;
+ *                       columns n..ld_t-1 zero).  colsum holds the sums over
+ *                       all n_total rows (summed over the blocks by the
+ *                       caller).
+ * gmgm_preprocess is the two steps on one block (n_total = n).
+ * Errors: GMGM_E_ARG (shapes, strides, n_total < n). */
+int gmgm_colsum_log1p(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, double* colsum,
+                      int accumulate);
+int gmgm_centre(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, const double* colsum,
+                int64_t n_total, float* x_out, int64_t ldx, uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t);
 
 /* ---- step 1: Gram ------------------------------------------------------- */
 
@@ -475,6 +528,17 @@ int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r,
                       uint32_t flags, int32_t* idx_out, float* val_out,
                       gmgm_topk_stats* stats);
 
+/* The rows [row0, row0 + m) of the network of gmgm_topk_network (the same
+ * V diag(psi) V^T, every column screened, the same readings, precision and
+ * certification): what one process of a row-sharded fit computes for the
+ * rows it owns, with V the full (all-gathered) vectors.
+ *   idx_out, val_out  device, m x k: row row0 + t of Psi in row t.
+ * 0 <= row0, 1 <= m, row0 + m <= d; other arguments as gmgm_topk_network
+ * (flags 0).  Errors: GMGM_E_ARG. */
+int gmgm_topk_network_rows(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
+                           const double* psi, int32_t k, gmgm_prec prec, int64_t row0, int64_t m,
+                           int32_t* idx_out, float* val_out, gmgm_topk_stats* stats);
+
 /* The network of a full-rank axis straight from its Gram: Psi = W diag(psi)
  * W^T with W the d x d orthonormal eigenvectors of S (psi[j] pairs with the
  * j-th largest eigenvalue of S; the axis' full spectrum).  As for
@@ -495,6 +559,31 @@ int gmgm_topk_network_gram(gmgm_handle* h, int64_t d, const double* S,
                            int64_t lds, const double* psi, int32_t k,
                            gmgm_prec prec, int32_t* idx_out, float* val_out,
                            gmgm_topk_stats* stats);
+
+/* Global top-n edges of an axis (Algorithm 1's last loop with the global
+ * threshold thresh_{n_l}; the appendix "Computational complexity" keeps the
+ * n_l strongest edges with a heap of size n_l), derived from its per-row
+ * top-k lists (as gmgm_topk_network writes them): the union of the lists as
+ * unordered pairs (i < j, the value listed by the lower row i when both
+ * rows list the pair), its n strongest by |value| descending, ties by (i, j)
+ * ascending.  The result is the global top-n of the network exactly when
+ * every row's k-th magnitude lies strictly below the n-th selected magnitude
+ * (no row can then hold an edge that strong outside its own list), or every
+ * list holds all d - 1 columns; *certified reports this.  A row whose list
+ * reaches that magnitude may hide more: rerun its rows with a larger k.
+ *   idx, val   device, d x k int32 / FP32 per-row lists (a list entry j < 0
+ *              or j == i is ignored).
+ *   n          1 <= n <= d k, n <= 2^30.
+ *   i_out, j_out, v_out  device, n int32 / int32 / FP32: the edges, by
+ *              |value| descending then (i, j).
+ *   count      host: the edges written (< n when the union holds fewer
+ *              distinct pairs; then *certified = 0).
+ *   certified  host: 1 if the edges are the network's global top-n.
+ * Synchronises the stream.  Errors: GMGM_E_ARG, GMGM_E_NOMEM,
+ * GMGM_E_CAND_OVERFLOW (more pairs tie at the n-th magnitude than the
+ * selection holds: at least 2n + 2 and 2^22). */
+int gmgm_topn_edges(gmgm_handle* h, int64_t d, int32_t k, const int32_t* idx, const float* val, int64_t n,
+                    int32_t* i_out, int32_t* j_out, float* v_out, int64_t* count, int* certified);
 
 #ifdef __cplusplus
 }

@@ -103,6 +103,14 @@ SIGNATURES = {
     "gmgm_warmstart_infer": (c_int, [c_vp, c_vp, c_vp, c_i32, c_vp, c_i32, c_dbl, c_vp, c_vp]),
     "gmgm_topk_network": (c_int, [c_vp, c_i64, c_i32, c_vp, c_int, c_i64, c_vp, c_i32, c_int,
                                   ctypes.c_uint32, c_vp, c_vp, ctypes.POINTER(TopkStats)]),
+    "gmgm_topk_network_rows": (c_int, [c_vp, c_i64, c_i32, c_vp, c_int, c_i64, c_vp, c_i32, c_int, c_i64, c_i64,
+                                       c_vp, c_vp, ctypes.POINTER(TopkStats)]),
+    "gmgm_peak_probe": (c_int, [c_vp, c_int, c_i64, ctypes.POINTER(c_dbl)]),
+    "gmgm_preprocess_csr": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp]),
+    "gmgm_colsum_log1p": (c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_vp, c_int]),
+    "gmgm_centre": (c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64]),
+    "gmgm_topn_edges": (c_int, [c_vp, c_i64, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, ctypes.POINTER(c_i64),
+                                ctypes.POINTER(c_int)]),
     "gmgm_topk_network_gram": (c_int, [c_vp, c_i64, c_vp, c_i64, c_vp, c_i32, c_int, c_vp, c_vp,
                                        ctypes.POINTER(TopkStats)]),
 }

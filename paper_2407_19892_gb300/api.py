@@ -114,6 +114,25 @@ def preprocess(counts: torch.Tensor, split: bool = True, inplace: bool = False, 
     return x, hi, lo, ld_t
 
 
+def preprocess_csr(indptr: torch.Tensor, indices: torch.Tensor, data: torch.Tensor, n: int, p: int,
+                   h: Handle = None):
+    """log1p + column centring of a CSR count matrix (n x p: int64 row
+    offsets, int32 ascending column indices, FP32 counts, on the GPU) straight
+    into the BF16 planes of X^T.  Returns (xt_hi, xt_lo, ld_t, column means
+    FP64)."""
+    h = h or handle(data.device)
+    _need_cuda(indptr, torch.int64, "indptr")
+    _need_cuda(indices, torch.int32, "indices")
+    _need_cuda(data, torch.float32, "data")
+    ld_t = ((n + 63) // 64) * 64
+    hi = torch.empty(p, ld_t, dtype=torch.bfloat16, device=data.device)
+    lo = torch.empty(p, ld_t, dtype=torch.bfloat16, device=data.device)
+    mu = torch.empty(p, dtype=torch.float64, device=data.device)
+    h.check(h.lib.gmgm_preprocess_csr(h.h, n, p, _ptr(indptr.contiguous()), _ptr(indices.contiguous()),
+                                      _ptr(data.contiguous()), _ptr(hi), _ptr(lo), ld_t, _ptr(mu)))
+    return hi, lo, ld_t, mu
+
+
 # ---- rank-based statistics (Nonparanormal Skeptic, COCA form) ----------------
 
 def skeptic(counts: torch.Tensor, axis: int, z: bool = True, planes: bool = True, ranks: bool = False,
@@ -200,16 +219,20 @@ def spectra(S: torch.Tensor, r: int, vectors: bool = True, rv: int = None, h: Ha
 
 
 def lift(x: torch.Tensor, W: torch.Tensor, E: torch.Tensor, r: int, xt_hi=None, xt_lo=None, ld_t: int = 0,
-         h: Handle = None):
+         rows: int = None, h: Handle = None):
     """U = X W_r diag(E_r)^-1/2 (rows x r, FP32).  With the BF16 planes of
     X^T (xt_hi, xt_lo, ld_t) and r <= 64 it runs on the tensor cores from
     them (3xBF16); otherwise from X in FP32."""
-    h = h or handle(x.device)
-    _need_cuda(x, torch.float32, "x")
+    dev = x.device if x is not None else xt_hi.device
+    h = h or handle(dev)
+    if x is not None:
+        _need_cuda(x, torch.float32, "x")
     W = W.contiguous()
     E = E.contiguous()
-    m = _matrix(x, xt_hi, xt_lo, ld_t)
-    U = torch.empty(x.shape[0], r, dtype=torch.float32, device=x.device)
+    if x is None and rows is None:
+        raise ValueError("without x, give the number of rows")
+    m = _matrix(x, xt_hi, xt_lo, ld_t, rows=rows, cols=W.shape[0])
+    U = torch.empty(m.rows, r, dtype=torch.float32, device=dev)
     h.check(h.lib.gmgm_lift(h.h, ctypes.byref(m), r, _ptr(W), W.stride(0), _ptr(E), _ptr(U), r))
     return U
 
@@ -276,6 +299,26 @@ def topk_network(V: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32,
     return idx, val, st.as_dict()
 
 
+def topk_network_rows(V: torch.Tensor, psi: torch.Tensor, k: int, row0: int, m: int, prec: int = L.FP32,
+                      h: Handle = None):
+    """Rows [row0, row0 + m) of the network of topk_network (every column
+    screened): idx int32 [m, k], val float32 [m, k], stats dict."""
+    h = h or handle(V.device)
+    if V.dtype not in (torch.float32, torch.float64) or not V.is_cuda:
+        raise ValueError("V must be a CUDA FP32/FP64 matrix")
+    if V.stride(1) != 1:
+        V = V.contiguous()
+    _need_cuda(psi, torch.float64, "psi")
+    d, r = V.shape
+    idx = torch.empty(m, k, dtype=torch.int32, device=V.device)
+    val = torch.empty(m, k, dtype=torch.float32, device=V.device)
+    st = L.TopkStats()
+    h.check(h.lib.gmgm_topk_network_rows(h.h, d, r, _ptr(V), int(V.dtype == torch.float64), V.stride(0),
+                                         _ptr(psi.contiguous()), k, prec, row0, m, _ptr(idx), _ptr(val),
+                                         ctypes.byref(st)))
+    return idx, val, st.as_dict()
+
+
 def topk_network_gram(S: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.FP32, h: Handle = None):
     """Network of a full-rank axis from its Gram S: top-k of |W diag(psi) W^T|
     with W the eigenvectors of S (psi in descending eigenvalue order); only
@@ -292,6 +335,27 @@ def topk_network_gram(S: torch.Tensor, psi: torch.Tensor, k: int, prec: int = L.
     h.check(h.lib.gmgm_topk_network_gram(h.h, d, _ptr(S), S.stride(0), _ptr(psi.contiguous()), k, prec, _ptr(idx),
                                          _ptr(val), ctypes.byref(st)))
     return idx, val, st.as_dict()
+
+
+def topn_edges(idx: torch.Tensor, val: torch.Tensor, n: int, h: Handle = None):
+    """Global top-n edges (i < j) from per-row top-k lists (d x k int32 /
+    FP32 on the GPU).  Returns (i, j, value, certified): the union's n
+    strongest pairs by |value| descending then (i, j), and whether they are
+    certified to be the network's global top-n."""
+    h = h or handle(idx.device)
+    _need_cuda(idx, torch.int32, "idx")
+    _need_cuda(val, torch.float32, "val")
+    idx, val = idx.contiguous(), val.contiguous()
+    d, k = idx.shape
+    io = torch.empty(n, dtype=torch.int32, device=idx.device)
+    jo = torch.empty(n, dtype=torch.int32, device=idx.device)
+    vo = torch.empty(n, dtype=torch.float32, device=idx.device)
+    cnt = ctypes.c_int64(0)
+    cert = ctypes.c_int(0)
+    h.check(h.lib.gmgm_topn_edges(h.h, d, k, _ptr(idx), _ptr(val), n, _ptr(io), _ptr(jo), _ptr(vo),
+                                  ctypes.byref(cnt), ctypes.byref(cert)))
+    c = cnt.value
+    return io[:c], jo[:c], vo[:c], bool(cert.value)
 
 
 # ---- the whole two-axis fit -----------------------------------------------------
@@ -316,14 +380,19 @@ class TwoAxisResult:
 
 def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols: int,
                  gram_prec: int = L.FP32, topk_prec: int = L.FP32, xt_hi=None, xt_lo=None, ld_t=0,
-                 tol: float = 1e-9, fp32_phase=True, init=None, warm_params=None,
+                 tol: float = 1e-9, fp32_phase=True, init=None, warm_params=None, rows: int = None,
                  h: Handle = None) -> TwoAxisResult:
     """Algorithm 1 on a centred matrix X (rows x cols, FP32, on the GPU):
     S_cols = X^T X, its eigenpairs (FP64), the row-axis vectors by the dual
     lift, the eigenvalue solve (from `init`, or from the learned start when
-    `warm_params` is given, else from 1/E), and both per-row top-k networks."""
-    h = h or handle(x.device)
-    S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, h=h)
+    `warm_params` is given, else from 1/E), and both per-row top-k networks.
+    x may be None when the BF16 planes of X^T are given (with `rows`), e.g.
+    from preprocess_csr."""
+    dev = x.device if x is not None else xt_hi.device
+    h = h or handle(dev)
+    n = x.shape[0] if x is not None else rows
+    p = x.shape[1] if x is not None else xt_hi.shape[0]
+    S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, rows=n, cols=p, h=h)
     rmax = max(r_rows, r_cols)
     full = r_cols == S.shape[0]
     # eigenvectors: the cell axis' r_rows for the lift; the gene axis' only
@@ -337,7 +406,7 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
         h.check(h.lib.gmgm_warmstart_infer(h.h, _ptr(warm_params), _ptr(e_rows), r_rows, _ptr(e_cols), r_cols,
                                            0.0, _ptr(i0), _ptr(i1)))
         init = [i0, i1]
-    v_rows = lift(x, W[:, :r_rows].contiguous(), e_rows, r_rows, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, h=h)
+    v_rows = lift(x, W[:, :r_rows].contiguous(), e_rows, r_rows, xt_hi=xt_hi, xt_lo=xt_lo, ld_t=ld_t, rows=n, h=h)
     (lam_rows, lam_cols), st = eigsolve([e_rows, e_cols], [(0, 1)], tol=tol, fp32_phase=fp32_phase,
                                         init=init, h=h)
     ir, vr, sr = topk_network(v_rows, lam_rows, k_rows, topk_prec, h=h)
@@ -346,6 +415,35 @@ def fit_two_axis(x: torch.Tensor, r_rows: int, r_cols: int, k_rows: int, k_cols:
     else:
         ic, vc, sc = topk_network(v_cols, lam_cols, k_cols, L.FP32, h=h)
     return TwoAxisResult(e_rows, v_rows, e_cols, v_cols, lam_rows, lam_cols, ir, vr, ic, vc, st, sr, sc, S)
+
+
+def fit_two_axis_skeptic(counts: torch.Tensor, r_rows: int, k_rows: int, k_cols: int, tol: float = 1e-9,
+                         h: Handle = None) -> TwoAxisResult:
+    """Algorithm 1 on rank-based statistics (Section "The model": the
+    Nonparanormal Skeptic; Section "Algorithm": its COCA form) of a count
+    matrix (cells x genes, FP32, on the GPU).  Each axis' Gram is the Gram of
+    its own normal scores: S_genes = Z_g^T Z_g with Z_g the scores of every
+    gene ranked over the cells; the cell axis from Z_c, every cell ranked over
+    its genes, through the dual Gram Z_c^T Z_c (its top r_rows eigenpairs)
+    and the lift U = Z_c W diag(E)^-1/2.  Then the solve (E_cells the top
+    eigenvalues, E_genes the full gene spectrum) and both networks.  Grams
+    in 3xBF16, the cell screen in BF16 (as the log1p fit)."""
+    h = h or handle(counts.device)
+    n, p = counts.shape
+    _, ghi, glo, ld_t, _ = skeptic(counts, L.AXIS_COLS, z=False, planes=True, h=h)
+    Sg = gram(None, L.SIDE_COLS, L.BF16X3, xt_hi=ghi, xt_lo=glo, ld_t=ld_t, rows=n, cols=p, h=h)
+    del ghi, glo
+    zc, chi, clo, ld_t, _ = skeptic(counts, L.AXIS_ROWS, planes=True, h=h)
+    del zc
+    Sc = gram(None, L.SIDE_COLS, L.BF16X3, xt_hi=chi, xt_lo=clo, ld_t=ld_t, rows=n, cols=p, h=h)
+    e_rows, Wc = spectra(Sc, r_rows, rv=r_rows, h=h)
+    U = lift(None, Wc, e_rows, r_rows, xt_hi=chi, xt_lo=clo, ld_t=ld_t, rows=n, h=h)
+    del chi, clo
+    e_cols, _ = spectra(Sg, p, vectors=False, h=h)
+    (lam_rows, lam_cols), st = eigsolve([e_rows, e_cols], [(0, 1)], tol=tol, h=h)
+    ir, vr, sr = topk_network(U, lam_rows, k_rows, L.BF16, h=h)
+    ic, vc, sc = topk_network_gram(Sg, lam_cols, k_cols, L.FP32, h=h)
+    return TwoAxisResult(e_rows, U, e_cols, None, lam_rows, lam_cols, ir, vr, ic, vc, st, sr, sc, Sg)
 
 
 # ---- several modalities sharing the cell axis; one K-axis tensor ---------------

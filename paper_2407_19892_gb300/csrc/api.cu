@@ -444,6 +444,89 @@ int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v
   return gmgm::topk_run(h, d, r, V, v_fp64, ldv, psi, k, prec, idx_out, val_out, h->scratch, stats);
 }
 
+int gmgm_topk_network_rows(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
+                           const double* psi, int32_t k, gmgm_prec prec, int64_t row0, int64_t m,
+                           int32_t* idx_out, float* val_out, gmgm_topk_stats* stats) {
+  if (!h) return GMGM_E_ARG;
+  if (d < 2 || r < 1 || !V || !psi || !idx_out || !val_out || ldv < r)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network_rows: need d >= 2, r >= 1, ldv >= r, non-null buffers");
+  if (k < 1 || k > 32 || k >= d) return fail(h, GMGM_E_ARG, "gmgm_topk_network_rows: need 1 <= k <= 32, k < d");
+  if (d > (int64_t(1) << 31) - 1 || r > 4096) return fail(h, GMGM_E_ARG, "gmgm_topk_network_rows: d >= 2^31 or r > 4096");
+  if (row0 < 0 || m < 1 || row0 + m > d) return fail(h, GMGM_E_ARG, "gmgm_topk_network_rows: need 0 <= row0, m >= 1, row0 + m <= d");
+  if (prec != GMGM_FP32 && prec != GMGM_BF16)
+    return fail(h, GMGM_E_ARG, "gmgm_topk_network_rows: prec must be FP32 or BF16");
+  if (prec != GMGM_FP32 && r > 64) return fail(h, GMGM_E_ARG, "gmgm_topk_network_rows: tensor-core screen supports r <= 64");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, gmgm::topk_scratch_bytes(d, r, k, prec));
+  if (rc) return rc;
+  return gmgm::topk_run(h, d, r, V, v_fp64, ldv, psi, k, prec, idx_out, val_out, h->scratch, stats, row0, m);
+}
+
+int gmgm_peak_probe(gmgm_handle* h, int kind, int64_t iters, double* rate) {
+  if (!h) return GMGM_E_ARG;
+  if ((kind != GMGM_PROBE_FP64 && kind != GMGM_PROBE_SFU) || iters < 1 || iters > (int64_t(1) << 24) || !rate)
+    return fail(h, GMGM_E_ARG, "gmgm_peak_probe: kind FP64 or SFU, 1 <= iters <= 2^24, non-null rate");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, 256);
+  if (rc) return rc;
+  return gmgm::peak_probe(h, kind, iters, rate);
+}
+
+int gmgm_preprocess_csr(gmgm_handle* h, int64_t n, int64_t p, const int64_t* indptr, const int32_t* indices,
+                        const float* data, uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t, double* colmean_out) {
+  if (!h) return GMGM_E_ARG;
+  if (n < 1 || p < 1 || p > 16384 || n > (int64_t(1) << 31) - 1 || !indptr || !indices || !data || !xt_hi ||
+      !xt_lo)
+    return fail(h, GMGM_E_ARG, "gmgm_preprocess_csr: need n >= 1, 1 <= p <= 16384, non-null buffers");
+  if (ld_t < n || ld_t % 64 != 0 || ((uintptr_t)xt_hi % 16) || ((uintptr_t)xt_lo % 16))
+    return fail(h, GMGM_E_ARG, "gmgm_preprocess_csr: ld_t must be >= n, a multiple of 64, 16-byte aligned planes");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, gmgm::preprocess_csr_scratch_bytes(p));
+  if (rc) return rc;
+  GMGM_CUDA_TRY(h, gmgm::launch_preprocess_csr(h, n, p, indptr, indices, data, xt_hi, xt_lo, ld_t, colmean_out));
+  return GMGM_OK;
+}
+
+int gmgm_colsum_log1p(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, double* colsum,
+                      int accumulate) {
+  if (!h) return GMGM_E_ARG;
+  if (n < 1 || p < 1 || !counts || !colsum || ldc < p)
+    return fail(h, GMGM_E_ARG, "gmgm_colsum_log1p: need n, p >= 1, ldc >= p, non-null buffers");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  GMGM_CUDA_TRY(h, gmgm::launch_colsum_log1p(h, n, p, counts, ldc, colsum, accumulate));
+  return GMGM_OK;
+}
+
+int gmgm_centre(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, const double* colsum,
+                int64_t n_total, float* x_out, int64_t ldx, uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t) {
+  if (!h) return GMGM_E_ARG;
+  if (n < 1 || p < 1 || n_total < n || !counts || !colsum || !x_out || ldc < p || ldx < p)
+    return fail(h, GMGM_E_ARG, "gmgm_centre: need 1 <= n <= n_total, p >= 1, ldc, ldx >= p, non-null buffers");
+  if ((const void*)counts == (const void*)x_out && ldc != ldx)
+    return fail(h, GMGM_E_ARG, "gmgm_centre: in-place needs ldx == ldc");
+  if ((xt_hi == nullptr) != (xt_lo == nullptr))
+    return fail(h, GMGM_E_ARG, "gmgm_centre: xt_hi and xt_lo must both be set or both NULL");
+  if (xt_hi && (ld_t < n || ld_t % 64 != 0 || ((uintptr_t)xt_hi % 16) || ((uintptr_t)xt_lo % 16)))
+    return fail(h, GMGM_E_ARG, "gmgm_centre: ld_t must be >= n, a multiple of 64, 16-byte aligned xt");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  GMGM_CUDA_TRY(h, gmgm::launch_centre(h, n, p, counts, ldc, colsum, n_total, x_out, ldx, xt_hi, xt_lo, ld_t));
+  return GMGM_OK;
+}
+
+int gmgm_topn_edges(gmgm_handle* h, int64_t d, int32_t k, const int32_t* idx, const float* val, int64_t n,
+                    int32_t* i_out, int32_t* j_out, float* v_out, int64_t* count, int* certified) {
+  if (!h) return GMGM_E_ARG;
+  if (d < 2 || d > (int64_t(1) << 31) - 1 || k < 1 || k >= d || !idx || !val || !i_out || !j_out || !v_out ||
+      !count || !certified)
+    return fail(h, GMGM_E_ARG, "gmgm_topn_edges: need 2 <= d < 2^31, 1 <= k < d, non-null buffers");
+  if (n < 1 || n > d * int64_t(k) || n > (int64_t(1) << 30))
+    return fail(h, GMGM_E_ARG, "gmgm_topn_edges: need 1 <= n <= d k, n <= 2^30");
+  GMGM_CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = gmgm::ensure_scratch(h, gmgm::topn_scratch_bytes(d, k, n));
+  if (rc) return rc;
+  return gmgm::topn_run(h, d, k, idx, val, n, i_out, j_out, v_out, count, certified);
+}
+
 int gmgm_topk_network_gram(gmgm_handle* h, int64_t d, const double* S, int64_t lds, const double* psi,
                            int32_t k, gmgm_prec prec, int32_t* idx_out, float* val_out, gmgm_topk_stats* stats) {
   if (!h) return GMGM_E_ARG;

@@ -64,6 +64,24 @@ cudaError_t launch_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float*
                               uint16_t* xt_lo, int64_t ld_t, double* colsum_scratch,
                               double* colmean_out);
 
+// throughput probes: kind 0 FP64 FMA (flop/s), 1 special-function unit
+// (reciprocal + base-2 logarithm operations/s)
+int peak_probe(gmgm_handle* h, int kind, long long iters, double* rate);
+
+// preprocessing of a CSR count matrix straight into the BF16 planes of X^T
+size_t preprocess_csr_scratch_bytes(int64_t p);
+cudaError_t launch_preprocess_csr(gmgm_handle* h, int64_t n, int64_t p, const int64_t* indptr, const int32_t* indices,
+                                  const float* data, uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t,
+                                  double* colmean_out);
+
+// row-split preprocessing: column sums of log1p over a row block, and the
+// centring of a row block by given column sums over n_total rows
+cudaError_t launch_colsum_log1p(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc,
+                                double* colsum, int accumulate);
+cudaError_t launch_centre(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc,
+                          const double* colsum, int64_t n_total, float* x_out, int64_t ldx, uint16_t* xt_hi,
+                          uint16_t* xt_lo, int64_t ld_t);
+
 cudaError_t launch_gram_fp32(gmgm_handle* h, const gmgm_matrix* m, int side, double* S,
                              int64_t lds, int accumulate, float* partials, int splits);
 int gram_fp32_splits(gmgm_handle* h, const gmgm_matrix* m, int side);
@@ -95,6 +113,11 @@ int skeptic_rows(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int6
 int skeptic_cols(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc, float* z, int64_t ldz,
                  uint16_t* hi, uint16_t* lo, int64_t ld_t, int32_t* ranks, int64_t ldr);
 
+// global top-n edges from per-row top-k lists
+size_t topn_scratch_bytes(int64_t d, int32_t k, int64_t n);
+int topn_run(gmgm_handle* h, int64_t d, int32_t k, const int32_t* idx, const float* val, int64_t n, int32_t* io,
+             int32_t* jo, float* vo, int64_t* count_out, int* certified_out);
+
 struct SolveDesc;  // defined in k_solve.cu
 size_t solve_scratch_bytes(const gmgm_problem* p);
 cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* const* init,
@@ -114,9 +137,10 @@ cudaError_t warmstart_infer(gmgm_handle* h, const float* P, const double* E0, in
                             double eps, double* l0, double* l1, void* scratch);
 
 size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec);
+// rows [row0, row0 + m) of Psi (m < 0: every row); idx, val hold m x k
 int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv,
              const double* psi, int32_t k, gmgm_prec prec, int32_t* idx, float* val,
-             void* scratch, gmgm_topk_stats* st);
+             void* scratch, gmgm_topk_stats* st, int64_t row0 = 0, int64_t m = -1);
 // V square (r == d) with orthonormal columns: Psi = c I + V diag(psi - c) V^T
 // with c = min psi; the network is that of the columns with psi > c
 size_t topk_ortho_scratch_bytes(int64_t d, int32_t r, int32_t k, gmgm_prec prec);

@@ -41,15 +41,17 @@ constexpr int kT = 64;
 
 // c and x may alias (in-place); each element is read and then written by
 // the same thread.
+// The mean of column j is colsum[j] / n_mean (n_mean = n, or the total row
+// count of a matrix whose rows are split over several calls).
 __global__ void centre_split_kernel(const float* c, int64_t n, int64_t p,
                                     int64_t ldc, float* x, int64_t ldx,
                                     __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                    int64_t ld_t, const double* __restrict__ colsum) {
+                                    int64_t ld_t, const double* __restrict__ colsum, int64_t n_mean) {
   __shared__ float tile[kT][kT + 1];
   const int64_t row0 = int64_t(blockIdx.x) * kT, col0 = int64_t(blockIdx.y) * kT;
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 256 threads: 64 x 4
   const int64_t col = col0 + tx;
-  const float mean = col < p ? float(colsum[col] / double(n)) : 0.f;
+  const float mean = col < p ? float(colsum[col] / double(n_mean)) : 0.f;
   for (int rr = ty; rr < kT; rr += 4) {
     const int64_t row = row0 + rr;
     float v = 0.f;
@@ -114,7 +116,7 @@ cudaError_t launch_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float*
   dim3 g2(unsigned((n + kT - 1) / kT), unsigned((p + kT - 1) / kT));
   centre_split_kernel<<<g2, 256, 0, s>>>(counts, n, p, ldc, x_out, ldx,
                                          reinterpret_cast<__nv_bfloat16*>(xt_hi),
-                                         reinterpret_cast<__nv_bfloat16*>(xt_lo), ld_t, colsum);
+                                         reinterpret_cast<__nv_bfloat16*>(xt_lo), ld_t, colsum, n);
   if (xt_hi && ld_t > n) {
     int blocks = int(std::min<int64_t>(4096, ((ld_t - n) * p + 255) / 256));
     zero_pad_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<__nv_bfloat16*>(xt_hi),
@@ -122,6 +124,35 @@ cudaError_t launch_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float*
   }
   if (colmean_out) colmean_kernel<<<unsigned((p + 255) / 256), 256, 0, s>>>(colsum, n, p, colmean_out);
   note_launch(2 + (xt_hi && ld_t > n ? 1 : 0) + (colmean_out ? 1 : 0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colsum_log1p(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc,
+                                double* colsum, int accumulate) {
+  cudaStream_t s = h->stream;
+  if (!accumulate) {
+    cudaError_t e = cudaMemsetAsync(colsum, 0, size_t(p) * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g1(unsigned((n + kRowChunk - 1) / kRowChunk), unsigned((p + kColThreads - 1) / kColThreads));
+  colsum_log1p_kernel<<<g1, kColThreads, 0, s>>>(counts, n, p, ldc, colsum);
+  note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_centre(gmgm_handle* h, int64_t n, int64_t p, const float* counts, int64_t ldc,
+                          const double* colsum, int64_t n_total, float* x_out, int64_t ldx, uint16_t* xt_hi,
+                          uint16_t* xt_lo, int64_t ld_t) {
+  cudaStream_t s = h->stream;
+  dim3 g2(unsigned((n + kT - 1) / kT), unsigned((p + kT - 1) / kT));
+  centre_split_kernel<<<g2, 256, 0, s>>>(counts, n, p, ldc, x_out, ldx, reinterpret_cast<__nv_bfloat16*>(xt_hi),
+                                         reinterpret_cast<__nv_bfloat16*>(xt_lo), ld_t, colsum, n_total);
+  if (xt_hi && ld_t > n) {
+    int blocks = int(std::min<int64_t>(4096, ((ld_t - n) * p + 255) / 256));
+    zero_pad_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<__nv_bfloat16*>(xt_hi),
+                                           reinterpret_cast<__nv_bfloat16*>(xt_lo), n, p, ld_t);
+  }
+  note_launch(1 + (xt_hi && ld_t > n ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -233,8 +233,8 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
                                const int32_t* __restrict__ cidx, const float* __restrict__ cval,
                                const float* __restrict__ thr, int nl, int64_t lstride,
                                const unsigned* __restrict__ colmax_bits, double u, int32_t* __restrict__ idx_out,
-                               float* __restrict__ val_out, int* __restrict__ flag_list, int* __restrict__ flag_count,
-                               unsigned* __restrict__ err_bits) {
+                               float* __restrict__ val_out, int64_t orow0, int* __restrict__ flag_list,
+                               int* __restrict__ flag_count, unsigned* __restrict__ err_bits) {
   extern __shared__ dfl rs_psi[];  // [r] psi as double-float, then [r] |psi| rounded up (FP32)
   float* psi_up = reinterpret_cast<float*>(rs_psi + r);
   for (int q = threadIdx.x; q < r; q += blockDim.x) {
@@ -349,8 +349,8 @@ __global__ void rescore_kernel(int64_t d, int r, const void* V, int v64, int64_t
     const float rhs = __fadd_ru(t, bnd);
     const bool certified = t < 0.f || qk.h > rhs || (qk.h == rhs && qk.l > 0.f);
     if (lane < k) {
-      idx_out[i * k + lane] = kj == INT_MAX ? -1 : kj;
-      val_out[i * k + lane] = sv;
+      idx_out[(i - orow0) * k + lane] = kj == INT_MAX ? -1 : kj;
+      val_out[(i - orow0) * k + lane] = sv;
     }
     if (!certified && lane == 0) {
       const int pos = atomicAdd(flag_count, 1);
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(kExThreads) exact_merge_kernel(const int* __re
                                                                   int k, const double* __restrict__ part_v,
                                                                   const int* __restrict__ part_j,
                                                                   int32_t* __restrict__ idx_out,
-                                                                  float* __restrict__ val_out) {
+                                                                  float* __restrict__ val_out, int64_t orow0) {
   extern __shared__ double msm[];
   const int rl = blockIdx.x;
   const int64_t i = rows[row0 + rl];
@@ -468,8 +468,8 @@ __global__ void __launch_bounds__(kExThreads) exact_merge_kernel(const int* __re
     if (threadIdx.x == 0) {
       const int e = bp[0];
       const bool ok = e >= 0 && pj[e] >= 0;
-      idx_out[i * k + out] = ok ? pj[e] : -1;
-      val_out[i * k + out] = ok ? float(pv[e]) : 0.f;
+      idx_out[(i - orow0) * k + out] = ok ? pj[e] : -1;
+      val_out[(i - orow0) * k + out] = ok ? float(pv[e]) : 0.f;
       if (e >= 0) key[e] = -2.0;
     }
     __syncthreads();
@@ -498,21 +498,21 @@ double screen_unit(gmgm_prec prec, int r) {
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
                     const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
                     const float* thr, int nl, int64_t lstride, int64_t m, const unsigned* colmax_bits, double u,
-                    int32_t* idx, float* val, int* flag_list, int* flag_count, unsigned* err_bits) {
+                    int32_t* idx, float* val, int64_t orow0, int* flag_list, int* flag_count, unsigned* err_bits) {
   // one warp per row; the grid covers at most m rows (grid-stride beyond)
   const unsigned blocks = unsigned(std::min<int64_t>((m * 32 + 255) / 256, 4096));
   const size_t smem = size_t(r) * (sizeof(dfl) + sizeof(float));  // <= 96 KB (r <= 8192)
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   rescore_kernel<<<blocks, 256, smem, s>>>(d, r, V, v64, ldv, psi, k, rows, m, count_dev, cidx, cval, thr, nl, lstride,
-                                        colmax_bits, u, idx, val, flag_list, flag_count, err_bits);
+                                        colmax_bits, u, idx, val, orow0, flag_list, flag_count, err_bits);
 }
 
 // Exact FP64 top-k of the listed rows, column-parallel: a row's columns are
 // split into chunks (one CTA each), then merged.  Batched so the partial
 // lists stay within kExactCap entries.
 int run_exact_rows(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
-                   const int* rows, int nrows, double* part_v, int* part_j, int32_t* idx, float* val) {
+                   const int* rows, int nrows, double* part_v, int* part_j, int32_t* idx, float* val, int64_t orow0) {
   if (nrows <= 0) return GMGM_OK;
   const int64_t chunk = std::max<int64_t>(8192, (d + 255) / 256);
   const int nchunks = int((d + chunk - 1) / chunk);
@@ -527,7 +527,7 @@ int run_exact_rows(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int
     exact_chunk_kernel<<<grid, kExThreads, smem, h->stream>>>(d, r, V, v64, ldv, psi, k, rows, row0, nb, nchunks,
                                                              chunk, part_v, part_j);
     exact_merge_kernel<<<unsigned(nb), kExThreads, msmem, h->stream>>>(rows, row0, nchunks, k, part_v, part_j, idx,
-                                                                      val);
+                                                                      val, orow0);
     note_launch(2);
   }
   GMGM_CUDA_TRY(h, cudaGetLastError());
@@ -545,11 +545,18 @@ size_t topk_scratch_bytes(int64_t d, int32_t r, int32_t /*k*/, gmgm_prec prec) {
   b += Carve::round(size_t(kExactCap) * 12) + 256;  // exact partial lists
   b += Carve::round(64);                        // counters
   b += Carve::round(topk_tc_scratch_bytes(d, r, prec));
+  b += Carve::round(size_t(d) * 4);             // row list of a block of rows
   return b + 4096;
 }
 
+__global__ void iota_kernel(int* __restrict__ out, int64_t m, int64_t base) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = int(base + i);
+}
+
 int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, int64_t ldv, const double* psi,
-             int32_t k, gmgm_prec prec, int32_t* idx, float* val, void* scratch, gmgm_topk_stats* st) {
+             int32_t k, gmgm_prec prec, int32_t* idx, float* val, void* scratch, gmgm_topk_stats* st, int64_t row0,
+             int64_t m) {
   cudaStream_t s = h->stream;
   const int rpad = ((r + kBK - 1) / kBK) * kBK;
   Carve c(scratch);
@@ -568,6 +575,13 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   int* part_j = c.take<int>(kExactCap);
   int* counters = c.take<int>(16);
   void* tc_scratch = c.take<char>(topk_tc_scratch_bytes(d, r, prec));
+  // a block of rows: its rows listed (screens, rescoring and the exact scan
+  // take row lists; outputs are written m x k from row row0)
+  const bool block = m >= 0;
+  if (!block) m = d;
+  int* rowlist = block ? c.take<int>(size_t(m)) : nullptr;
+  if (block)
+    iota_kernel<<<unsigned(std::min<int64_t>((m + 255) / 256, 4096)), 256, 0, s>>>(rowlist, m, row0);
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (st)
     for (auto& e : ev) cudaEventCreate(&e);
@@ -588,13 +602,15 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   GMGM_CUDA_TRY(h, cudaFuncSetAttribute(screen_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const unsigned sblocks = unsigned(std::min<int64_t>((d + kBM - 1) / kBM, int64_t(h->num_sms) * 2));
   if (prec == GMGM_FP32) {
-    screen_fp32_kernel<<<sblocks, 256, smem, s>>>(A, B, d, rpad, nullptr, d, nullptr, cidx, cval, thr);
+    screen_fp32_kernel<<<sblocks, 256, smem, s>>>(A, B, d, rpad, rowlist, m, nullptr, cidx, cval, thr);
   } else {
-    GMGM_CUDA_TRY(h, launch_screen_tc(h, d, r, V, v_fp64, ldv, psi, prec, cidx, cval, thr, tc_scratch));
+    GMGM_CUDA_TRY(h, launch_screen_tc(h, d, r, V, v_fp64, ldv, psi, prec, cidx, cval, thr, tc_scratch,
+                                      block ? row0 : 0, m, rowlist));
   }
   if (st) cudaEventRecord(ev[1], s);
-  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, nullptr, nullptr, cidx, cval, thr, nl, d, d, colmax,
-                 screen_unit(prec, r), idx, val, flag1, counters + 0, reinterpret_cast<unsigned*>(counters + 2));
+  launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, rowlist, nullptr, cidx, cval, thr, nl, m, m, colmax,
+                 screen_unit(prec, r), idx, val, block ? row0 : 0, flag1, counters + 0,
+                 reinterpret_cast<unsigned*>(counters + 2));
   note_launch(prec == GMGM_FP32 ? 4 : 2);
   // rows the screen could not certify (the count is read back once to size
   // the work): after the BF16 screen, a 3xBF16 tensor-core screen of those
@@ -609,14 +625,15 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     GMGM_CUDA_TRY(h, launch_screen_tc_repair(h, d, r, V, v_fp64, ldv, psi, flag1, nflag, ncs, cidx, cval, thr,
                                              tc_scratch));
     launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, flag1, nullptr, cidx, cval, thr, 2 * ncs, nflag, nflag, colmax,
-                   screen_unit(GMGM_BF16X3, r), idx, val, flag2, counters + 4,
+                   screen_unit(GMGM_BF16X3, r), idx, val, block ? row0 : 0, flag2, counters + 4,
                    reinterpret_cast<unsigned*>(counters + 2));
     note_launch(1);
     GMGM_CUDA_TRY(h, cudaMemcpyAsync(&nexact, counters + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
     GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
     exact_rows = flag2;
   }
-  int rc = run_exact_rows(h, d, r, V, v_fp64, ldv, psi, k, exact_rows, nexact, part_v, part_j, idx, val);
+  int rc = run_exact_rows(h, d, r, V, v_fp64, ldv, psi, k, exact_rows, nexact, part_v, part_j, idx, val,
+                          block ? row0 : 0);
   if (rc) return rc;
   if (st) cudaEventRecord(ev[2], s);
   GMGM_CUDA_TRY(h, cudaGetLastError());

@@ -165,8 +165,8 @@ __device__ __forceinline__ void sub_min(const float* lv, int sub, float& mv, int
 
 // The published minimum carries the row block it belongs to (high word), so
 // a partner still in the previous row block is never mistaken for this one.
-__device__ __noinline__ ListState offer(float* lv, int* li, float* smv, int* smp, unsigned long long* pub, unsigned tag,
-                                        ListState st, float v, int j) {
+__device__ __forceinline__ ListState offer_body(float* lv, int* li, float* smv, int* smp, unsigned long long* pub,
+                                                unsigned tag, ListState st, float v, int j) {
   if (st.cnt < kC) {
     lv[st.cnt * kLists] = v;
     li[st.cnt * kLists] = j;
@@ -202,6 +202,12 @@ __device__ __noinline__ ListState offer(float* lv, int* li, float* smv, int* smp
   return st;
 }
 
+// Out of line for the inserts made with a tile's values still in registers.
+__device__ __noinline__ ListState offer(float* lv, int* li, float* smv, int* smp, unsigned long long* pub, unsigned tag,
+                                        ListState st, float v, int j) {
+  return offer_body(lv, li, smv, smp, pub, tag, st, v, j);
+}
+
 __device__ __forceinline__ float partner_min(const volatile unsigned long long* partner, unsigned tag) {
   const unsigned long long pv = *partner;
   return unsigned(pv >> 32) == tag ? __uint_as_float(unsigned(pv)) : -1.f;
@@ -230,17 +236,32 @@ __device__ __forceinline__ ListState insert_chunk(const uint32_t (&v)[32], int s
   return st;
 }
 
-// A stashed chunk (shared memory) through insert_chunk.
+// A stashed chunk (shared memory): the winners read back by index, the
+// inserts inline (the tile's registers are free here).
 __device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int self, int n, float* lv, int* li, float* smv,
                                         int* smp, unsigned long long* pub, const volatile unsigned long long* partner,
                                         unsigned tag, ListState st, float floor_v) {
-  uint32_t v[32];
+  float thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
+  uint32_t mask = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const uint4 w = reinterpret_cast<const uint4*>(slot)[k];
-    v[4 * k] = w.x, v[4 * k + 1] = w.y, v[4 * k + 2] = w.z, v[4 * k + 3] = w.w;
+    mask |= (fabsf(__uint_as_float(w.x)) > thr ? 1u : 0u) << (4 * k);
+    mask |= (fabsf(__uint_as_float(w.y)) > thr ? 1u : 0u) << (4 * k + 1);
+    mask |= (fabsf(__uint_as_float(w.z)) > thr ? 1u : 0u) << (4 * k + 2);
+    mask |= (fabsf(__uint_as_float(w.w)) > thr ? 1u : 0u) << (4 * k + 3);
   }
-  return insert_chunk(v, sj, self, n, lv, li, smv, smp, pub, partner, tag, st, floor_v);
+  while (mask) {
+    const int e = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const float x = fabsf(__uint_as_float(slot[e]));
+    const int j = sj + e;
+    if (x > thr && j < n && j != self) {
+      st = offer_body(lv, li, smv, smp, pub, tag, st, x, j);
+      thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
+    }
+  }
+  return st;
 }
 
 // max |v| over one 32-value chunk (four short chains).
@@ -626,7 +647,8 @@ int screen_tc_slices(int64_t m, int num_sms, int64_t cap_rows) {
 }
 
 cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi,
-                             gmgm_prec prec, int32_t* cidx, float* cval, float* thr, void* scratch) {
+                             gmgm_prec prec, int32_t* cidx, float* cval, float* thr, void* scratch, int64_t row0,
+                             int64_t m, const int* rows) {
   if (prec != GMGM_BF16 || r > kKP || d > (int64_t(1) << 30)) return cudaErrorNotSupported;
   Carve c(scratch);
   __nv_bfloat16* A = c.take<__nv_bfloat16>(size_t(d) * kKP);
@@ -637,7 +659,9 @@ cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, in
     prep_tc_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, A, B);
   }
   note_launch(2);
-  return run_screen<256, 1, true, 16>(h, A, nullptr, int(d), B, nullptr, int(d), 1, nullptr, r, cidx, cval, thr);
+  // rows [row0, row0 + m): their A rows are contiguous from row row0
+  return run_screen<256, 1, true, 16>(h, A + row0 * kKP, nullptr, int(m), B, nullptr, int(d), 1, rows, r, cidx, cval,
+                                      thr);
 }
 
 cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,

@@ -48,15 +48,17 @@ double screen_unit(gmgm_prec prec, int r);
 void launch_rescore(cudaStream_t s, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi, int k,
                     const int* rows, const int* count_dev, const int32_t* cidx, const float* cval,
                     const float* thr, int nl, int64_t lstride, int64_t m, const unsigned* colmax_bits, double u,
-                    int32_t* idx, float* val, int* flag_list, int* flag_count, unsigned* err_bits);
+                    int32_t* idx, float* val, int64_t orow0, int* flag_list, int* flag_count, unsigned* err_bits);
 
 // tensor-core screens: BF16 over all rows; 3xBF16 over m listed rows in ncs
 // column slices (candidate arrays hold ncs * m list pairs)
 size_t topk_tc_scratch_bytes(int64_t d, int r, gmgm_prec prec);
 int screen_tc_slices(int64_t m, int num_sms, int64_t cap_rows);
+// (the rows [row0, row0 + m) of Psi, listed in `rows`, or every row when
+// rows is null)
 cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,
                              const double* psi, gmgm_prec prec, int32_t* cidx, float* cval, float* thr,
-                             void* scratch);
+                             void* scratch, int64_t row0, int64_t m, const int* rows);
 cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,
                                     const double* psi, const int* rows, int m, int ncs, int32_t* cidx, float* cval,
                                     float* thr, void* scratch);

@@ -1,10 +1,10 @@
-"""Layout of the fit over several GPUs: independent replicas.
+"""Layout of the benchmark over several GPUs: independent replicas.
 
-The fit of one dataset has no exchange step (every stage of Algorithm 1
-works on that dataset's own Gram, spectra and eigenvalues), so N GPUs run N
-independent fits, one process per GPU, each on its own dataset: weak scaling
-with no collective on the data path.  The only collectives are the barrier
-around the timed region and the maximum of the per-rank step times.
+The benchmark's N-GPU run fits N datasets, one process per GPU, each on its
+own dataset: weak scaling with no collective on the data path.  The only
+collectives are the barrier around the timed region and the maximum of the
+per-rank step times.  (One dataset's fit split over GPUs by cells, with its
+all-reduce, broadcasts and all-gather, is ``sharded.py``.)
 """
 
 import os

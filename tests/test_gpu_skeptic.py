@@ -125,3 +125,37 @@ def test_argument_errors(g, cuda_dev):
         hi = torch.empty(4, 64, dtype=torch.bfloat16, device=cuda_dev)
         h.check(h.lib.gmgm_skeptic(h.h, 10, 4, c.data_ptr(), 4, 0, None, 0, hi.data_ptr(), hi.data_ptr(), 64,
                                    None, 0))
+
+
+def test_skeptic_fit_matches_the_oracle(g, cuda_dev):
+    # the two-axis fit on rank-based statistics: each axis' Gram from its own
+    # normal scores (genes ranked over cells, cells ranked over genes)
+    from oracle.recon import topk_gap, topk_rows
+    from oracle.solve import solve_newton, two_axis_problem
+    from oracle.spectra import dual_lift, top_eigh
+    n, p, r, k = 3000, 200, 15, 10
+    counts = scrna_counts(n, p, 6, seed=20240802).numpy().astype(np.float64)
+    res = g.fit_two_axis_skeptic(torch.from_numpy(counts.astype(np.float32)).to(cuda_dev), r, k, k)
+    zc = osk.normal_scores(counts)          # cells ranked over genes
+    zg = osk.normal_scores(counts.T)        # genes ranked over cells
+    e_c, w_c = top_eigh(zc.T @ zc, r)
+    e_g, _ = top_eigh(zg @ zg.T, p)
+    np.testing.assert_allclose(res.e_rows.cpu().numpy(), e_c, rtol=5e-5)
+    np.testing.assert_allclose(res.e_cols.cpu().numpy(), e_g, rtol=0, atol=5e-5 * e_g[0])
+    lam, info = solve_newton(two_axis_problem(e_c, e_g))
+    sr = lam[:r][:, None] + lam[r:][None, :]
+    sg = res.lam_rows.cpu().numpy()[:, None] + res.lam_cols.cpu().numpy()[None, :]
+    assert np.max(np.abs(sg - sr) / sr) <= 1e-4
+    # the lifted cell vectors: U = Z_c W diag(E)^-1/2 (signs free)
+    U = res.v_rows.cpu().numpy()
+    ref = dual_lift(zc, w_c, e_c)
+    sign = np.sign(np.sum(U * ref, axis=0))
+    assert np.max(np.abs(U - ref * sign[None, :])) <= 1e-4 * np.abs(ref).max()
+    # the cell network stage-wise on its own vectors
+    lr = res.lam_rows.cpu().numpy()
+    V = U.astype(np.float64)
+    ri, _ = topk_rows(V, lr, k)
+    gap = topk_gap(V, lr, k)
+    idx = res.idx_rows.cpu().numpy()
+    ok = gap > 1e-5
+    assert np.array_equal(np.sort(idx[ok], 1), np.sort(ri[ok], 1)) and ok.mean() > 0.5
