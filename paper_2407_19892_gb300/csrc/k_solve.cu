@@ -53,6 +53,12 @@ struct Params {
   double tol;
   int max_newton, max_cg, fp32_phase, gauge, has_init;
   double trace_rtol;
+  // several CTAs (cooperative launch): CTA 0 runs the method and hands each
+  // grid pass to every CTA through these words (null with one CTA)
+  unsigned* co_bar;   // grid barrier words
+  int* co_cmd;        // the pass kind, -1: finished
+  double* co_ls;      // line-search sum of the pass
+  int* co_bad;        // a point of the pass was infeasible / non-finite
 };
 
 struct Vecs {
@@ -94,7 +100,7 @@ __device__ double modality_pass(const Params& P, const Vecs& V, int gm, double* 
   double ls = 0.0;
   if (k == 1) {
     const int a = P.ma[gm][0];
-    for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.r[a]; i += gridDim.x * blockDim.x) {
       const int ia = P.off[a] + i;
       if (KIND == K_GRAD64) {
         const double s = V.x[ia];
@@ -137,7 +143,8 @@ __device__ double modality_pass(const Params& P, const Vecs& V, int gm, double* 
   const float* xa32 = V.x32 + P.off[a];
   const float* va32 = V.v32 + P.off[a];
   const double* xa64 = V.x + P.off[a];
-  for (int64_t c0 = 0; c0 < R; c0 += kChunkCols) {
+  // the chunks of rest points are split over the CTAs
+  for (int64_t c0 = int64_t(blockIdx.x) * kChunkCols; c0 < R; c0 += int64_t(gridDim.x) * kChunkCols) {
     // this thread's rest points in the chunk
     int64_t qi[kQ];
     float xb[kQ], vb[kQ];
@@ -232,7 +239,7 @@ __device__ double modality_pass(const Params& P, const Vecs& V, int gm, double* 
           rem /= P.r[ax];
           const int ci = P.off[ax] + idx;
           const double v1 = KIND == K_GRAD64 ? acc64[q] : double(acc1[q]);
-          if (nrest == 1) {
+          if (nrest == 1 && gridDim.x == 1) {
             V.s1[ci] += v1;  // owned by this thread
             if (KIND == K_GRAD32) V.s2[ci] += double(acc2[q]);
           } else {
@@ -246,27 +253,94 @@ __device__ double modality_pass(const Params& P, const Vecs& V, int gm, double* 
   __syncthreads();
   if (KIND != K_LS) {
     for (int i = threadIdx.x; i < ra; i += blockDim.x) {
-      V.s1[P.off[a] + i] += sm1[i];
-      if (KIND == K_GRAD32) V.s2[P.off[a] + i] += sm2[i];
+      if (gridDim.x == 1) {
+        V.s1[P.off[a] + i] += sm1[i];
+        if (KIND == K_GRAD32) V.s2[P.off[a] + i] += sm2[i];
+      } else {
+        atomicAdd(&V.s1[P.off[a] + i], sm1[i]);
+        if (KIND == K_GRAD32) atomicAdd(&V.s2[P.off[a] + i], sm2[i]);
+      }
     }
   }
   __syncthreads();
   return ls;
 }
 
+// This CTA's share of one pass over every modality's grid.
 template <int KIND>
-__device__ double grid_pass(const Params& P, const Vecs& V, double* sm1, double* sm2, double* red, int* bad) {
+__device__ double pass_share(const Params& P, const Vecs& V, double* sm1, double* sm2, int* bad) {
+  double ls = 0.0;
+  for (int gm = 0; gm < P.nmod; ++gm) ls += modality_pass<KIND>(P, V, gm, sm1, sm2, bad);
+  __syncthreads();
+  return ls;
+}
+
+// A pass over the grids, by CTA 0.  With several CTAs it zeroes the sums,
+// publishes the pass kind, meets the others at a grid barrier, does its
+// share, and collects the line-search sum and the infeasible flag after a
+// second barrier (a barrier that gives up marks the pass infeasible).
+template <int KIND>
+__device__ double grid_pass(const Params& P, const Vecs& V, double* sm1, double* sm2, double* red, int* bad,
+                            unsigned& epoch, int* status) {
   if (KIND != K_LS) {
     for (int i = threadIdx.x; i < P.N; i += blockDim.x) {
       V.s1[i] = 0.0;
       if (KIND == K_GRAD32) V.s2[i] = 0.0;
     }
   }
+  if (gridDim.x == 1) {
+    __syncthreads();
+    const double ls = pass_share<KIND>(P, V, sm1, sm2, bad);
+    return KIND == K_LS ? block_sum(ls, red) : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<volatile int*>(P.co_cmd) = KIND;
+    *reinterpret_cast<volatile double*>(P.co_ls) = 0.0;
+    *reinterpret_cast<volatile int*>(P.co_bad) = 0;
+  }
+  if (!grid_barrier(P.co_bar, gridDim.x, epoch, status)) {
+    if (threadIdx.x == 0) *bad = 1;
+    __syncthreads();
+    return 0.0;
+  }
+  double ls = pass_share<KIND>(P, V, sm1, sm2, bad);
+  if (KIND == K_LS) {
+    ls = block_sum(ls, red);
+    if (threadIdx.x == 0) atomicAdd(P.co_ls, ls);
+  }
+  if (!grid_barrier(P.co_bar, gridDim.x, epoch, status)) {
+    if (threadIdx.x == 0) *bad = 1;
+    __syncthreads();
+    return 0.0;
+  }
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(P.co_bad)) *bad = 1;
   __syncthreads();
-  double ls = 0.0;
-  for (int gm = 0; gm < P.nmod; ++gm) ls += modality_pass<KIND>(P, V, gm, sm1, sm2, bad);
-  __syncthreads();
-  return KIND == K_LS ? block_sum(ls, red) : 0.0;
+  return KIND == K_LS ? *reinterpret_cast<volatile double*>(P.co_ls) : 0.0;
+}
+
+// CTAs 1.. of a cooperative solve: take every pass CTA 0 publishes, do their
+// share, until CTA 0 publishes the end (or a grid barrier gives up).
+__device__ void pass_worker(const Params& P, const Vecs& V, double* sm1, double* sm2, int* status) {
+  __shared__ double wred[33];
+  __shared__ int wbad;
+  unsigned epoch = 0;
+  for (;;) {
+    if (!grid_barrier(P.co_bar, gridDim.x, epoch, status)) return;
+    const int k = *reinterpret_cast<volatile int*>(P.co_cmd);
+    if (k < 0) return;
+    if (threadIdx.x == 0) wbad = 0;
+    __syncthreads();
+    if (k == K_GRAD32) pass_share<K_GRAD32>(P, V, sm1, sm2, &wbad);
+    else if (k == K_GRAD64) pass_share<K_GRAD64>(P, V, sm1, sm2, &wbad);
+    else if (k == K_HVP) pass_share<K_HVP>(P, V, sm1, sm2, &wbad);
+    else {
+      const double ls = block_sum(pass_share<K_LS>(P, V, sm1, sm2, &wbad), wred);
+      if (threadIdx.x == 0) atomicAdd(P.co_ls, ls);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && wbad) atomicOr(P.co_bad, 1);
+    if (!grid_barrier(P.co_bar, gridDim.x, epoch, status)) return;
+  }
 }
 
 __device__ double dotv(const double* a, const double* b, int n, double* red) {
@@ -285,10 +359,8 @@ __device__ double rel_kkt(const Params& P, const Vecs& V, double* red) {
   return block_max(m, red);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, int* status, gmgm_solve_stats* st) {
-  extern __shared__ double smem[];
-  double* sm1 = smem;
-  double* sm2 = smem + kMaxLoop;
+__device__ void solve_master(const Params& P, const Vecs& V, int* status, gmgm_solve_stats* st, double* sm1,
+                             double* sm2, unsigned& epoch) {
   __shared__ double red[33];
   __shared__ int bad_s;
   if (threadIdx.x == 0) bad_s = 0;
@@ -382,13 +454,13 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, in
     // ---- gradient (and Hessian diagonal) ----
     for (int i = threadIdx.x; i < N; i += blockDim.x) V.x32[i] = float(V.x[i]);
     __syncthreads();
-    grid_pass<K_GRAD32>(P, V, sm1, sm2, red, &bad_s);
+    grid_pass<K_GRAD32>(P, V, sm1, sm2, red, &bad_s, epoch, status);
     ++passes;
     if (fp64) {
       // FP64 gradient; s2 (Hessian diagonal) kept from the FP32 pass
       for (int i = threadIdx.x; i < N; i += blockDim.x) V.hd[i] = V.s2[i];
       __syncthreads();
-      grid_pass<K_GRAD64>(P, V, sm1, sm2, red, &bad_s);
+      grid_pass<K_GRAD64>(P, V, sm1, sm2, red, &bad_s, epoch, status);
       ++passes;
       for (int i = threadIdx.x; i < N; i += blockDim.x) V.g[i] = V.E[i] - V.s1[i];
     } else {
@@ -428,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, in
     for (int it = 0; it < P.max_cg && gnorm > 0.0; ++it) {
       for (int i = threadIdx.x; i < N; i += blockDim.x) V.v32[i] = float(V.p[i]);
       __syncthreads();
-      grid_pass<K_HVP>(P, V, sm1, sm2, red, &bad_s);
+      grid_pass<K_HVP>(P, V, sm1, sm2, red, &bad_s, epoch, status);
       ++passes;
       ++cg_total;
       for (int i = threadIdx.x; i < N; i += blockDim.x) V.hp[i] = V.act[i] ? 0.0 : V.s1[i];
@@ -464,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, in
       if (threadIdx.x == 0) bad_s = 0;
       __syncthreads();
       const double gdx = dotv(V.g, V.dx, N, red);
-      const double rem = grid_pass<K_LS>(P, V, sm1, sm2, red, &bad_s);
+      const double rem = grid_pass<K_LS>(P, V, sm1, sm2, red, &bad_s, epoch, status);
       ++passes;
       const int infeasible = bad_s;
       __syncthreads();
@@ -518,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, in
     for (int i = threadIdx.x; i < P.r[a]; i += blockDim.x) P.out[a][i] = V.x[P.off[a] + i];
   for (int i = threadIdx.x; i < N; i += blockDim.x) V.x32[i] = float(V.x[i]);
   __syncthreads();
-  grid_pass<K_GRAD64>(P, V, sm1, sm2, red, &bad_s);
+  grid_pass<K_GRAD64>(P, V, sm1, sm2, red, &bad_s, epoch, status);
   for (int i = threadIdx.x; i < N; i += blockDim.x) V.g[i] = V.E[i] - V.s1[i];
   __syncthreads();
   const double kkt64 = rel_kkt(P, V, red);
@@ -559,12 +631,31 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, in
   }
 }
 
+
+// One CTA runs the method; with a cooperative launch (large grids) CTAs
+// 1.. take a share of every grid pass.
+__global__ void __launch_bounds__(kThreads, 1) solve_kernel(Params P, Vecs V, int* status, gmgm_solve_stats* st) {
+  extern __shared__ double smem[];
+  double* sm1 = smem;
+  double* sm2 = smem + kMaxLoop;
+  if (blockIdx.x > 0) {
+    pass_worker(P, V, sm1, sm2, status);
+    return;
+  }
+  unsigned epoch = 0;
+  solve_master(P, V, status, st, sm1, sm2, epoch);
+  if (gridDim.x > 1) {
+    if (threadIdx.x == 0) *reinterpret_cast<volatile int*>(P.co_cmd) = -1;
+    grid_barrier(P.co_bar, gridDim.x, epoch, status);
+  }
+}
+
 }  // namespace
 
 size_t solve_scratch_bytes(const gmgm_problem* p) {
   int64_t N = 0;
   for (int a = 0; a < p->n_axes; ++a) N += p->r[a];
-  return size_t(N) * (13 * sizeof(double) + 2 * sizeof(float) + sizeof(int)) + 20 * 256;
+  return size_t(N) * (13 * sizeof(double) + 2 * sizeof(float) + sizeof(int)) + 22 * 256;
 }
 
 cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* const* init,
@@ -621,6 +712,29 @@ cudaError_t launch_solve(gmgm_handle* h, const gmgm_problem* p, const double* co
   const size_t smem = size_t(2) * kMaxLoop * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
+  // grids of 2^20 points or more: every SM takes a share of each pass
+  int64_t pts = 0;
+  for (int g = 0; g < P.nmod; ++g) {
+    int64_t q = 1;
+    for (int k = 0; k < P.mk[g]; ++k) q *= P.r[P.ma[g][k]];
+    pts = std::max(pts, q);
+  }
+  int per_sm = 0;
+  if (pts >= (int64_t(1) << 20) &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, kThreads, smem) == cudaSuccess &&
+      per_sm >= 1) {
+    P.co_bar = h->d_barrier;
+    P.co_cmd = c.take<int>(4);
+    P.co_ls = c.take<double>(2);
+    P.co_bad = P.co_cmd + 1;
+    if ((e = cudaMemsetAsync(h->d_barrier, 0, 16, h->stream)) != cudaSuccess) return e;
+    gmgm_solve_stats* stp = d_stats;
+    int* status = h->d_status;
+    void* args[] = {&P, &V, &status, &stp};
+    e = cudaLaunchCooperativeKernel((void*)solve_kernel, dim3(h->num_sms), dim3(kThreads), args, smem, h->stream);
+    note_launch(1);
+    return e;
+  }
   solve_kernel<<<1, kThreads, smem, h->stream>>>(P, V, h->d_status, d_stats);
   note_launch(1);
   return cudaGetLastError();

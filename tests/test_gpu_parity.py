@@ -594,3 +594,13 @@ def test_topk_network_rows_equals_the_rows_of_the_full_network(g, cuda_dev, prec
         assert st["screen_err_ratio"] <= 1.0
     with pytest.raises(g.GmgmError):
         g.topk_network_rows(V, psi, k, 2500, 501, p)
+
+
+def test_eigsolve_grid_over_a_million_points_uses_every_sm(g, cuda_dev):
+    # a 1100 x 1000 grid (1.1e6 points): the passes are split over all SMs
+    # (cooperative launch); the result must equal the oracle's as for the
+    # one-CTA solve
+    rng = _rng(97)
+    E = [np.sort(rng.uniform(0.5, 3.0, 1100))[::-1].copy(), np.sort(rng.uniform(0.2, 4.0, 1000))[::-1].copy()]
+    err, st, got, prob = _solve_case(g, cuda_dev, E, [(0, 1)])
+    assert err <= 1e-7, (err, st)
