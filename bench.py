@@ -197,6 +197,22 @@ def kernel_traffic(kernel_file, kernel_name):
     return None
 
 
+def screen_executed_tflops(st, n, r):
+    """TFLOP/s of the BF16 cell screen on the work it executed: the 128 x 256
+    tiles it multiplied (one dense sweep plus its sampling pass, as counted by
+    the kernel), 2 * 128 * 256 * r flop each (K = r: the padding of K to a
+    multiple of 16 is not counted).  Falls back to 2 n^2 r when no tile count
+    is reported."""
+    tiles = int(st.get("screen_tiles", 0) or 0)
+    if tiles > 0:
+        flops = 2.0 * 128 * 256 * r * tiles
+        work = f"{tiles} tiles of 128 x 256 x r (dense sweep {int(st['screen_tiles_dense'])} + sampling pass)"
+    else:
+        flops = 2.0 * n * n * r
+        work = "2 n^2 r (dense)"
+    return flops / (st["screen_ms"] / 1e3) / 1e12, work
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -348,11 +364,11 @@ def other_workload(a):
     roof = None
     st = res.topk_stats[0] if hasattr(res, "topk_stats") else res.topk_rows_stats
     if a.workload != "tensor3" and st and st.get("screen_ms", 0) > 0:
-        flops = 2.0 * units * units * (50 if a.workload == "multimodal" else a.r_cells)
-        ach = flops / (st["screen_ms"] / 1e3) / 1e12
+        r_scr = 50 if a.workload == "multimodal" else a.r_cells
+        ach, work = screen_executed_tflops(st, units, r_scr)
         roof = {"bound": "tensor", "kernel": "screen_tc_kernel", "achieved": ach, "peak": pk["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops_sustained"],
-                "peak_source": f"{pk_kind} bf16 sustained", "traffic": None}
+                "peak_source": f"{pk_kind} bf16 sustained", "work": work, "traffic": None}
         detail["screen_ms"] = st["screen_ms"]
     if a.workload == "tensor3":
         sv = res.solve
@@ -588,6 +604,11 @@ def main():
     flops = 2.0 * a.cells * a.cells * a.r_cells
     scr_ms = statistics.mean(screen_ms)
     achieved_tflops = flops / (scr_ms / 1e3) / 1e12
+    work = "2 n^2 r (dense)"
+    if topk_prec != g.FP32:
+        st_s = dict(res.topk_rows_stats)
+        st_s["screen_ms"] = scr_ms
+        achieved_tflops, work = screen_executed_tflops(st_s, a.cells, a.r_cells)
     if topk_prec == g.FP32:
         # FP32 SIMT: 152 SMs x 128 FMA lanes x 2 flop x max SM clock
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -598,7 +619,7 @@ def main():
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "kernel": "screen_tc_kernel", "achieved": achieved_tflops, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved_tflops / peak, "peak_source": f"{pk_kind} bf16 sustained",
-                "traffic": kernel_traffic("k_topk_tc.cu", "screen_tc_kernel")}
+                "work": work, "traffic": kernel_traffic("k_topk_tc.cu", "screen_tc_kernel")}
 
     if rank != 0:
         if world > 1:

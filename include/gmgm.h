@@ -483,6 +483,10 @@ typedef struct {
   double rescore_ms;         /* device time of rescoring (+ repair) */
   double screen_err_ratio;   /* max over candidates of |screened - exact| /
                                 the screen's error bound (<= 1 expected) */
+  int64_t screen_tiles;      /* GMGM_BF16: 128 x 256 tiles the first screen
+                                multiplied (sampling pass included) */
+  int64_t screen_tiles_dense; /* GMGM_BF16: tiles of one dense sweep
+                                 (row blocks x column tiles) */
 } gmgm_topk_stats;
 
 /* Per-row top-k of Psi = V diag(psi) V^T without forming Psi (Algorithm 1:

@@ -65,7 +65,8 @@ MLP_PARAMS = 256 * 132 + 256 + 256 * 256 + 256 + 128 * 256 + 128
 
 class TopkStats(ctypes.Structure):
     _fields_ = [("rows_uncertified", c_i64), ("rows_exact", c_i64), ("candidates", c_i64),
-                ("screen_ms", c_dbl), ("rescore_ms", c_dbl), ("screen_err_ratio", c_dbl)]
+                ("screen_ms", c_dbl), ("rescore_ms", c_dbl), ("screen_err_ratio", c_dbl),
+                ("screen_tiles", c_i64), ("screen_tiles_dense", c_i64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -605,7 +605,8 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     screen_fp32_kernel<<<sblocks, 256, smem, s>>>(A, B, d, rpad, rowlist, m, nullptr, cidx, cval, thr);
   } else {
     GMGM_CUDA_TRY(h, launch_screen_tc(h, d, r, V, v_fp64, ldv, psi, prec, cidx, cval, thr, tc_scratch,
-                                      block ? row0 : 0, m, rowlist));
+                                      block ? row0 : 0, m, rowlist,
+                                      reinterpret_cast<unsigned long long*>(counters + 8)));
   }
   if (st) cudaEventRecord(ev[1], s);
   launch_rescore(s, d, r, V, v_fp64, ldv, psi, k, rowlist, nullptr, cidx, cval, thr, nl, m, m, colmax,
@@ -638,8 +639,8 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
   if (st) cudaEventRecord(ev[2], s);
   GMGM_CUDA_TRY(h, cudaGetLastError());
   if (st) {
-    unsigned hc[4] = {0, 0, 0, 0};
-    GMGM_CUDA_TRY(h, cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, s));
+    unsigned hc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    GMGM_CUDA_TRY(h, cudaMemcpyAsync(hc, counters, 40, cudaMemcpyDeviceToHost, s));
     GMGM_CUDA_TRY(h, cudaStreamSynchronize(s));
     float t1 = 0.f, t2 = 0.f;
     cudaEventElapsedTime(&t1, ev[0], ev[1]);
@@ -652,6 +653,10 @@ int topk_run(gmgm_handle* h, int64_t d, int32_t r, const void* V, int v_fp64, in
     st->screen_ms = t1;
     st->rescore_ms = t2;
     st->screen_err_ratio = double(e1);
+    unsigned long long nrun;
+    memcpy(&nrun, &hc[8], 8);
+    st->screen_tiles = prec == GMGM_BF16 ? int64_t(nrun) : 0;
+    st->screen_tiles_dense = prec == GMGM_BF16 ? ((m + 127) / 128) * ((d + 255) / 256) : 0;
     for (auto& e : ev) cudaEventDestroy(e);
   }
   return GMGM_OK;

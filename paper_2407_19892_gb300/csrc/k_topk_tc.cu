@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     screen_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int m, int n,
                      int ncs, const int* __restrict__ rows, int ksteps, int32_t* __restrict__ cand_idx,
-                     float* __restrict__ cand_val, float* __restrict__ thr_out, int* __restrict__ status) {
+                     float* __restrict__ cand_val, float* __restrict__ thr_out, int* __restrict__ status,
+                     unsigned long long* __restrict__ tiles_run) {
   using S = Screen<TN, NP, STASH>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -430,6 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // drain: every MMA issued so far has completed once `done` fires
       tc::mma_commit(&bs->done);
       tc::mbar_wait(&bs->done, 0, kSpin);
+      if (tiles_run) atomicAdd(tiles_run, static_cast<unsigned long long>(used));
     }
   } else {
     // ---------------- epilogue ----------------
@@ -607,7 +609,8 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int boxrows) {
 
 template <int TN, int NP, bool STASH, int SAMP>
 cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, const void* bh, const void* bl, int n,
-                       int ncs, const int* rows, int r, int32_t* cidx, float* cval, float* thr) {
+                       int ncs, const int* rows, int r, int32_t* cidx, float* cval, float* thr,
+                       unsigned long long* tiles_run = nullptr) {
   CUtensorMap mah, mal, mbh, mbl;
   if (!make_map(&mah, ah, m, kTM) || !make_map(&mbh, bh, n, TN)) return cudaErrorInvalidValue;
   mal = mah;
@@ -620,7 +623,7 @@ cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, co
   const int items = int((m + kTM - 1) / kTM) * ncs;
   const int grid = std::min(items, h->num_sms);
   kern<<<grid, kThreads, smem, h->stream>>>(mah, mal, mbh, mbl, m, n, ncs, rows, (r + 15) / 16, cidx, cval, thr,
-                                            h->d_status);
+                                            h->d_status, tiles_run);
   return cudaGetLastError();
 }
 
@@ -648,7 +651,7 @@ int screen_tc_slices(int64_t m, int num_sms, int64_t cap_rows) {
 
 cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv, const double* psi,
                              gmgm_prec prec, int32_t* cidx, float* cval, float* thr, void* scratch, int64_t row0,
-                             int64_t m, const int* rows) {
+                             int64_t m, const int* rows, unsigned long long* tiles_run) {
   if (prec != GMGM_BF16 || r > kKP || d > (int64_t(1) << 30)) return cudaErrorNotSupported;
   Carve c(scratch);
   __nv_bfloat16* A = c.take<__nv_bfloat16>(size_t(d) * kKP);
@@ -661,7 +664,7 @@ cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, in
   note_launch(2);
   // rows [row0, row0 + m): their A rows are contiguous from row row0
   return run_screen<256, 1, true, 16>(h, A + row0 * kKP, nullptr, int(m), B, nullptr, int(d), 1, rows, r, cidx, cval,
-                                      thr);
+                                      thr, tiles_run);
 }
 
 cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,

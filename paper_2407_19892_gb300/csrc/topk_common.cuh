@@ -58,7 +58,8 @@ int screen_tc_slices(int64_t m, int num_sms, int64_t cap_rows);
 // rows is null)
 cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,
                              const double* psi, gmgm_prec prec, int32_t* cidx, float* cval, float* thr,
-                             void* scratch, int64_t row0, int64_t m, const int* rows);
+                             void* scratch, int64_t row0, int64_t m, const int* rows,
+                             unsigned long long* tiles_run);  // (may be null) += B tiles multiplied
 cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void* V, int v64, int64_t ldv,
                                     const double* psi, const int* rows, int m, int ncs, int32_t* cidx, float* cval,
                                     float* thr, void* scratch);

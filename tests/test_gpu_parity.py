@@ -596,6 +596,22 @@ def test_topk_network_rows_equals_the_rows_of_the_full_network(g, cuda_dev, prec
         g.topk_network_rows(V, psi, k, 2500, 501, p)
 
 
+def test_topk_bf16_screen_counts_its_tiles(g, cuda_dev):
+    # the screen reports the 128 x 256 tiles it multiplied: one dense sweep
+    # (row blocks x column tiles) plus the sampling pass over every 16th
+    # tile of each row block (the roofline is taken on this executed work)
+    rng = _rng(62)
+    d, r, k = 40000, 50, 10
+    V = torch.from_numpy(rng.standard_normal((d, r)).astype(np.float32)).to(cuda_dev)
+    lam = torch.from_numpy(rng.uniform(0.1, 2.0, r)).to(cuda_dev)
+    _, _, st = g.topk_network(V, lam, k, prec=g.BF16)
+    nrb, nt = (d + 127) // 128, (d + 255) // 256
+    assert st["screen_tiles_dense"] == nrb * nt
+    assert st["screen_tiles"] == nrb * (nt + (nt + 15) // 16), st
+    _, _, st32 = g.topk_network(V, lam, k, prec=g.FP32)
+    assert st32["screen_tiles"] == 0 and st32["screen_tiles_dense"] == 0
+
+
 def test_eigsolve_grid_over_a_million_points_uses_every_sm(g, cuda_dev):
     # a 1100 x 1000 grid (1.1e6 points): the passes are split over all SMs
     # (cooperative launch); the result must equal the oracle's as for the
