@@ -263,6 +263,16 @@ typedef struct {
  * leading dimension lds; both triangles are written.  Partial sums are
  * formed in `prec` arithmetic and combined in FP64.  GMGM_SIDE_ROWS supports
  * GMGM_FP32 only.  Errors: GMGM_E_ARG (shape/stride/precision). */
+/* Why one matrix per call rather than a list of labelled tensors: every
+ * axis Gram of a tensor is the Gram of a matricization, and each of those
+ * is one strided matrix or one batch of equally strided slices (the three
+ * forms above), so the tensor bookkeeping (which index is which axis, which
+ * modalities share it) stays with the caller, and the sum over modalities
+ * or over row blocks of cells (a sharded fit) is `accumulate`.  A tensor of
+ * order four or more is reached the same way: its axis-l matricization is a
+ * batch of (product of the leading extents) slices of d_l x (product of the
+ * trailing extents); only the batch form's single level of batching is
+ * built in, so the caller loops over the outer indices with accumulate = 1. */
 int gmgm_gram(gmgm_handle* h, const gmgm_matrix* m, int side, gmgm_prec prec,
               double* S, int64_t lds, int accumulate);
 
@@ -406,7 +416,10 @@ int gmgm_eigsolve(gmgm_handle* h, const gmgm_problem* p,
  *   - Arguments as gmgm_eigsolve.  `stats` (host, optional): if non-NULL the
  *     call synchronises the stream, fills it and returns its status.
  *     Otherwise device-detected problems are only visible in the returned
- *     lambda values (the status word is private to this entry point). */
+ *     lambda values (the status word is private to this entry point).
+ *   - The array's device address is looked up on every call (a lookup, not
+ *     an allocation), so the entry point stays valid after a device reset
+ *     reloads the module. */
 int gmgm_eigsolve_static(const gmgm_problem* p, const double* const* init,
                          const gmgm_solve_opts* opts, double* const* lambda_out,
                          gmgm_solve_stats* stats, void* cuda_stream);
@@ -526,6 +539,11 @@ typedef struct {
  * Errors: GMGM_E_ARG. */
 #define GMGM_TOPK_ORTHO 1u
 
+/* One V serves both the screen and the rescoring (no separate FP64 copy for
+ * rescoring): the screen rounds V to its own arithmetic internally, and the
+ * rescoring reads V as given (an FP64 V is rescored in FP64, an FP32 V in
+ * double-float from its exact FP32 values), so the lists are exact for the
+ * V the caller passed and a second copy would only duplicate memory. */
 int gmgm_topk_network(gmgm_handle* h, int64_t d, int32_t r,
                       const void* V, int v_fp64, int64_t ldv,
                       const double* psi, int32_t k, gmgm_prec prec,

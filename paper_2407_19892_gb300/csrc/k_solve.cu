@@ -24,7 +24,6 @@
 
 #include <algorithm>
 #include <cfloat>
-#include <mutex>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -771,22 +770,17 @@ static __device__ __align__(256) unsigned char g_solve_static[kStaticBytes];
 
 namespace {
 
-std::mutex g_static_mu;
-void* g_static_addr[128] = {};  // per device: device address of g_solve_static
-
-// First call on a device: look up the array's device address (once).
+// The array's device address on the current device, looked up on every call
+// (no allocation; a cached address would dangle after a device reset
+// reloads the module).
 int static_scratch(int device, void** out) {
-  if (device < 0 || device >= 128) return GMGM_E_ARG;
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_addr[device]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_solve_static) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return GMGM_E_CUDA;
-    }
-    g_static_addr[device] = ptr;
+  if (device < 0) return GMGM_E_ARG;
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_solve_static) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return GMGM_E_CUDA;
   }
-  *out = g_static_addr[device];
+  *out = ptr;
   return GMGM_OK;
 }
 
