@@ -264,17 +264,23 @@ __device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int self, 
   return st;
 }
 
-// max |v| over one 32-value chunk (four short chains).
+// max(|a|, |b|, |c|): the three-input max of sm_100 and later with the
+// absolute-value modifier (one instruction).
+__device__ __forceinline__ float amax3(float a, float b, float c) {
+  float d;
+  asm("max.abs.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// max |v| over one 32-value chunk: a tree of 16 three-input maxima.
 __device__ __forceinline__ float chunk_absmax(const uint32_t (&v)[32]) {
-  float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  float t[11];
 #pragma unroll
-  for (int e = 0; e < 32; e += 4) {
-    m0 = fmaxf(m0, fabsf(__uint_as_float(v[e + 0])));
-    m1 = fmaxf(m1, fabsf(__uint_as_float(v[e + 1])));
-    m2 = fmaxf(m2, fabsf(__uint_as_float(v[e + 2])));
-    m3 = fmaxf(m3, fabsf(__uint_as_float(v[e + 3])));
-  }
-  return fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+  for (int q = 0; q < 10; ++q)
+    t[q] = amax3(__uint_as_float(v[3 * q]), __uint_as_float(v[3 * q + 1]), __uint_as_float(v[3 * q + 2]));
+  t[10] = amax3(__uint_as_float(v[30]), __uint_as_float(v[31]), t[0]);
+  const float u0 = amax3(t[1], t[2], t[3]), u1 = amax3(t[4], t[5], t[6]), u2 = amax3(t[7], t[8], t[9]);
+  return amax3(u0, u1, fmaxf(u2, t[10]));
 }
 
 // Epilogue warp: wait for accumulator buffer accu & 1, pull this warp's lane
