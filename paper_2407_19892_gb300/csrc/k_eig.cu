@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
   __shared__ dfl red[33];
   const unsigned nb = gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int gwarp = blockIdx.x * nwarps + warp, total_warps = nb * nwarps;
+  // rows go to CTAs round-robin first (row i: CTA i mod nb), so every SM
+  // streams its share of a short trailing block too
+  const int gwarp = warp * int(nb) + blockIdx.x, total_warps = nb * nwarps;
   const int gthread = blockIdx.x * blockDim.x + threadIdx.x, total_threads = nb * blockDim.x;
   const double unscale = ldexp(1.0, scale_exp(amax));
   unsigned epoch = 0;  // grid barriers passed
