@@ -13,20 +13,18 @@
 //   warp 1      MMA issuer (one thread): per B tile D[128 x TN] = A B^T
 //               (K = 64 in four K=16 steps), FP32 in TMEM, double-buffered;
 //   warps 2-9   epilogue: two threads per row (one per half of the tile's
-//               columns), each with a kC-slot candidate list; tcgen05.ld 32
-//               columns at a time, one max per element against the pair's
-//               shared threshold, and only when it is beaten a per-lane insert
-//               (a bitmask of the winners, values pulled out of registers by a
-//               select tree).
-// A list is four sub-lists of 8 slots with their minima cached, so replacing
-// the list's minimum rescans 8 slots, not 32.  In the main screen inserts are
-// rare and scattered over the lanes, so a lane that hits a chunk parks the
-// chunk's 32 values in a shared-memory stash (one slot per thread) instead of
-// inserting at once; after each tile the warp drains the stashes together
-// once 8 lanes have one (a lane whose slot is taken inserts at once).  The
-// pair's threshold is the larger of the two lists' minima (each list
-// publishes its minimum in shared memory once full); a stale read only admits
-// more candidates.
+//               columns), each owning a kC-slot candidate list; tcgen05.ld.red
+//               (sm_103a) brings 32 columns at a time together with their
+//               largest magnitude, so a chunk costs one compare against the
+//               list's threshold.
+// A chunk that beats its row's threshold is merged by the whole warp: the
+// owning lane stages its 32 values in shared memory, each lane takes one,
+// and the winners enter the row's list, which is kept sorted over the lanes
+// (lane c holds slot c; a ballot finds each winner's position and the lanes
+// below it shift down one slot).  The threshold of a (row, half) list is the
+// larger of its own minimum and its partner's (each list publishes its
+// minimum in shared memory once full); a stale read only admits more
+// candidates.
 // Threshold floor (main screen, long sweeps): a sampling pass over every
 // 16th B tile first keeps, per (row, half), the 6 largest 32-column chunk
 // maxima in registers (a branch-free insert per chunk); the 6th of them is a
@@ -34,12 +32,12 @@
 // the half lie above it, so a list fills with values that mostly stay: the
 // inserts of a random-order sweep (about kC ln(n / kC) per list) drop to
 // about kC ln 3.  Every column left out of a row's two lists has a screened
-// value <= the larger of the floor and the final minima.  Each row gets 2 kC candidates and two
-// thresholds; the rescore keeps the kC largest screened values and folds the
-// largest dropped one into the row's certification threshold.  All CTAs sweep
-// the B tiles in the same order (L2 reuse).  Every wait is bounded; on
-// timeout the kernel records GMGM_DEV_TIMEOUT and leaves after freeing its
-// TMEM.
+// value <= the larger of the floor and the final minima.  Each row gets
+// 2 kC candidates and two thresholds; the rescore keeps the kC largest
+// screened values and folds the largest dropped one into the row's
+// certification threshold.  All CTAs sweep the B tiles in the same order (L2
+// reuse).  Every wait is bounded; on timeout the kernel records
+// GMGM_DEV_TIMEOUT and leaves after freeing its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -61,11 +59,7 @@ constexpr size_t kSmemCap = 232448;          // dynamic shared memory per CTA
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kATile = kTM * kKP * 2;        // 16 KB per plane
-constexpr int kSub = 8;                      // slots per sub-list
-constexpr int kNSub = kC / kSub;             // sub-lists per list
 constexpr int kLists = 2 * kTM;              // (row, half) lists per CTA
-constexpr int kSlot = 36;                    // stash slot stride (words): 32 values, 16-byte aligned, 4-way banks
-constexpr int kBatch = 8;                    // stashed lanes that trigger a drain
 constexpr unsigned kFull = 0xffffffffu;
 constexpr long long kSpin = 1ll << 23;       // polls per bounded wait
 constexpr int kSampK = 6;                    // chunk maxima kept by the sampling pass
@@ -96,19 +90,19 @@ struct __align__(8) Bars {
   int abort;
 };
 
-// TN columns per B tile; NP products per K step (1: BF16, 3: split);
-// STASH: park hit chunks for batched inserts.  The B ring takes as many
-// stages (up to kMaxStages) as the shared memory left over holds.
-template <int TN, int NP, bool STASH>
+// TN columns per B tile; NP products per K step (1: BF16, 3: split).  The B
+// ring takes as many stages (up to kMaxStages) as the shared memory left
+// over holds.
+template <int TN, int NP>
 struct Screen {
   static constexpr int kTN = TN;
   static constexpr int kChunks = TN / 64;                 // 32-column chunks per half
   static constexpr int kPlanes = NP == 3 ? 2 : 1;         // hi (+ lo)
   static constexpr int kBTile = TN * kKP * 2;             // per plane
   static constexpr int kTmemCols = 2 * TN;
-  static constexpr size_t kLists_ = size_t(2) * kC * kLists * 4 + size_t(2) * kNSub * kLists * 4 + size_t(kLists) * 8;
-  static constexpr size_t kStash = STASH ? size_t(32) * kEpiWarps * kSlot * 4 : 0;
-  static constexpr size_t kFixed = 1024 /*align slack*/ + size_t(kPlanes) * kATile + kLists_ + kStash + sizeof(Bars);
+  // lists (values, columns), published minima, one 32-value staging row per epilogue warp
+  static constexpr size_t kLists_ = size_t(2) * kC * kLists * 4 + size_t(kLists) * 8 + size_t(kEpiWarps) * 32 * 4;
+  static constexpr size_t kFixed = 1024 /*align slack*/ + size_t(kPlanes) * kATile + kLists_ + sizeof(Bars);
   static constexpr int kStages = int((kSmemCap - kFixed) / (size_t(kPlanes) * kBTile)) < kMaxStages
                                      ? int((kSmemCap - kFixed) / (size_t(kPlanes) * kBTile))
                                      : kMaxStages;
@@ -127,168 +121,48 @@ __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
 
 __device__ __forceinline__ bool aborted(Bars* bs) { return *reinterpret_cast<volatile int*>(&bs->abort) != 0; }
 
-// One (row, half) candidate list, slot-major (stride kLists): fill, then
-// replace the minimum.  Slots [8s, 8s+8) form sub-list s, whose minimum and
-// its slot sit in smv/smp (also slot-major).  Out of line (inserts are
-// rare); state by value.
-struct ListState {
-  int cnt;
-  int minsub;  // sub-list holding the minimum
-  float minv;  // minimum once full, else -1
-};
-
-// r[e] for a per-lane runtime e without leaving registers: a 5-level select
-// tree over constant indices (31 selects).
-__device__ __forceinline__ uint32_t pick32(const uint32_t (&r)[32], int e) {
-  uint32_t a[16], b[8], c[4], d[2];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) a[q] = (e & 16) ? r[q + 16] : r[q];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) b[q] = (e & 8) ? a[q + 8] : a[q];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) c[q] = (e & 4) ? b[q + 4] : b[q];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) d[q] = (e & 2) ? c[q + 2] : c[q];
-  return (e & 1) ? d[1] : d[0];
-}
-
-// Minimum (value, slot) of sub-list sub.
-__device__ __forceinline__ void sub_min(const float* lv, int sub, float& mv, int& mp) {
-  mv = lv[(sub * kSub) * kLists];
-  mp = sub * kSub;
-#pragma unroll
-  for (int c = 1; c < kSub; ++c) {
-    const float x = lv[(sub * kSub + c) * kLists];
-    if (x < mv) mv = x, mp = sub * kSub + c;
-  }
-}
-
-// The published minimum carries the row block it belongs to (high word), so
-// a partner still in the previous row block is never mistaken for this one.
-__device__ __forceinline__ ListState offer_body(float* lv, int* li, float* smv, int* smp, unsigned long long* pub,
-                                                unsigned tag, ListState st, float v, int j) {
-  if (st.cnt < kC) {
-    lv[st.cnt * kLists] = v;
-    li[st.cnt * kLists] = j;
-    if (++st.cnt < kC) return st;
-#pragma unroll
-    for (int s = 0; s < kNSub; ++s) {
-      float mv;
-      int mp;
-      sub_min(lv, s, mv, mp);
-      smv[s * kLists] = mv;
-      smp[s * kLists] = mp;
-    }
-  } else {
-    const int s = st.minsub;
-    const int p = smp[s * kLists];
-    lv[p * kLists] = v;
-    li[p * kLists] = j;
-    float mv;
-    int mp;
-    sub_min(lv, s, mv, mp);
-    smv[s * kLists] = mv;
-    smp[s * kLists] = mp;
-  }
-  st.minv = smv[0];
-  st.minsub = 0;
-#pragma unroll
-  for (int s = 1; s < kNSub; ++s) {
-    const float x = smv[s * kLists];
-    if (x < st.minv) st.minv = x, st.minsub = s;
-  }
-  *reinterpret_cast<volatile unsigned long long*>(pub) =
-      (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(st.minv);  // publish for the partner
-  return st;
-}
-
-// Out of line for the inserts made with a tile's values still in registers.
-__device__ __noinline__ ListState offer(float* lv, int* li, float* smv, int* smp, unsigned long long* pub, unsigned tag,
-                                        ListState st, float v, int j) {
-  return offer_body(lv, li, smv, smp, pub, tag, st, v, j);
-}
-
 __device__ __forceinline__ float partner_min(const volatile unsigned long long* partner, unsigned tag) {
   const unsigned long long pv = *partner;
   return unsigned(pv >> 32) == tag ? __uint_as_float(unsigned(pv)) : -1.f;
 }
 
-// Insert the winners of one 32-value chunk (columns sj..sj+31) against the
-// current threshold; `self` is the row's own column (never an edge).
-__device__ __forceinline__ ListState insert_chunk(const uint32_t (&v)[32], int sj, int self, int n, float* lv, int* li,
-                                                  float* smv, int* smp, unsigned long long* pub,
-                                                  const volatile unsigned long long* partner, unsigned tag,
-                                                  ListState st, float floor_v) {
-  float thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
-  uint32_t mask = 0;
-#pragma unroll
-  for (int e = 0; e < 32; ++e) mask |= (fabsf(__uint_as_float(v[e])) > thr ? 1u : 0u) << e;
-  while (mask) {
-    const int e = __ffs(mask) - 1;
-    mask &= mask - 1;
-    const float x = fabsf(__uint_as_float(pick32(v, e)));
-    const int j = sj + e;
-    if (x > thr && j < n && j != self) {
-      st = offer(lv, li, smv, smp, pub, tag, st, x, j);
-      thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
-    }
+// Warp-cooperative insert into one (row, half) list.  The list is sorted in
+// descending order over the lanes: lane c holds slot c (value lv[Lr * kC +
+// c], column li[...]), empty slots hold -1, so slot 31 is the list's minimum
+// once it is full and -1 before.  Every lane offers at most one magnitude x
+// (column jx; -1 offers nothing); those above `thr` are inserted one by one
+// in lane order (a ballot finds the insertion position, the lanes below it
+// shift down one slot and the last slot falls out).  Returns the new
+// minimum.  Called by the whole warp.
+__device__ __forceinline__ float coop_insert(float* lv, int* li, int Lr, int lane, float x, int jx, float thr) {
+  float lval = lv[Lr * kC + lane];
+  int lidx = li[Lr * kC + lane];
+  unsigned w = __ballot_sync(kFull, x > thr);
+  while (w) {
+    const int e = __ffs(w) - 1;
+    w &= w - 1;
+    const float v = __shfl_sync(kFull, x, e);
+    const int j = __shfl_sync(kFull, jx, e);
+    if (v <= __shfl_sync(kFull, lval, 31)) continue;  // below the list's minimum by now (warp-uniform)
+    const int pos = __popc(__ballot_sync(kFull, lval >= v));
+    const float uv = __shfl_up_sync(kFull, lval, 1);
+    const int ui = __shfl_up_sync(kFull, lidx, 1);
+    if (lane > pos) lval = uv, lidx = ui;
+    if (lane == pos) lval = v, lidx = j;
   }
-  return st;
-}
-
-// A stashed chunk (shared memory): the winners read back by index, the
-// inserts inline (the tile's registers are free here).
-__device__ __noinline__ ListState drain(const uint32_t* slot, int sj, int self, int n, float* lv, int* li, float* smv,
-                                        int* smp, unsigned long long* pub, const volatile unsigned long long* partner,
-                                        unsigned tag, ListState st, float floor_v) {
-  float thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
-  uint32_t mask = 0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const uint4 w = reinterpret_cast<const uint4*>(slot)[k];
-    mask |= (fabsf(__uint_as_float(w.x)) > thr ? 1u : 0u) << (4 * k);
-    mask |= (fabsf(__uint_as_float(w.y)) > thr ? 1u : 0u) << (4 * k + 1);
-    mask |= (fabsf(__uint_as_float(w.z)) > thr ? 1u : 0u) << (4 * k + 2);
-    mask |= (fabsf(__uint_as_float(w.w)) > thr ? 1u : 0u) << (4 * k + 3);
-  }
-  while (mask) {
-    const int e = __ffs(mask) - 1;
-    mask &= mask - 1;
-    const float x = fabsf(__uint_as_float(slot[e]));
-    const int j = sj + e;
-    if (x > thr && j < n && j != self) {
-      st = offer_body(lv, li, smv, smp, pub, tag, st, x, j);
-      thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
-    }
-  }
-  return st;
-}
-
-// max(|a|, |b|, |c|): the three-input max of sm_100 and later with the
-// absolute-value modifier (one instruction).
-__device__ __forceinline__ float amax3(float a, float b, float c) {
-  float d;
-  asm("max.abs.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-  return d;
-}
-
-// max |v| over one 32-value chunk: a tree of 16 three-input maxima.
-__device__ __forceinline__ float chunk_absmax(const uint32_t (&v)[32]) {
-  float t[11];
-#pragma unroll
-  for (int q = 0; q < 10; ++q)
-    t[q] = amax3(__uint_as_float(v[3 * q]), __uint_as_float(v[3 * q + 1]), __uint_as_float(v[3 * q + 2]));
-  t[10] = amax3(__uint_as_float(v[30]), __uint_as_float(v[31]), t[0]);
-  const float u0 = amax3(t[1], t[2], t[3]), u1 = amax3(t[4], t[5], t[6]), u2 = amax3(t[7], t[8], t[9]);
-  return amax3(u0, u1, fmaxf(u2, t[10]));
+  lv[Lr * kC + lane] = lval;
+  li[Lr * kC + lane] = lidx;
+  return __shfl_sync(kFull, lval, 31);
 }
 
 // Epilogue warp: wait for accumulator buffer accu & 1, pull this warp's lane
 // quarter of the half's columns in one round trip, and hand the buffer back
-// to the MMA warp.  False (abort raised) when the wait gives up.
+// to the MMA warp.  mx[c] = max |r[c][e]| over chunk c, reduced by the
+// tensor-memory load itself (tcgen05.ld.red).  False (abort raised) when the
+// wait gives up.
 template <class S>
 __device__ __forceinline__ bool take_tile(Bars* bs, uint32_t tmem, int q, int half, long long accu, int lane,
-                                          int* status, uint32_t (&r)[S::kChunks][32]) {
+                                          int* status, uint32_t (&r)[S::kChunks][32], float (&mx)[S::kChunks]) {
   const int b = int(accu & 1);
   if (!__all_sync(kFull, tc::mbar_wait(&bs->accf[b], uint32_t(accu >> 1) & 1, kSpin))) {
     if (lane == 0) raise_abort(bs, status);
@@ -298,7 +172,7 @@ __device__ __forceinline__ bool take_tile(Bars* bs, uint32_t tmem, int q, int ha
   const uint32_t taddr = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * S::kTN + half * (S::kTN / 2));
   __syncwarp();
 #pragma unroll
-  for (int c = 0; c < S::kChunks; ++c) tc::tmem_ld_32x32b_x32(taddr + c * 32, r[c]);
+  for (int c = 0; c < S::kChunks; ++c) tc::tmem_ld_red_absmax_32x32b_x32(taddr + c * 32, r[c], mx[c]);
   tc::tmem_ld_wait();
   tc::fence_before_sync();
   __syncwarp();
@@ -309,28 +183,26 @@ __device__ __forceinline__ bool take_tile(Bars* bs, uint32_t tmem, int q, int ha
 // m rows of A (hi, lo planes) against n rows of B (hi, lo planes), the B
 // tiles split into ncs column slices; work item = (row block, slice).  Row p
 // of A is row rows[p] of Psi (p itself when rows is null); slice cs writes
-// its two lists of row p to cand_*[cs * m + p][2 kC] and their minima to
+// its two lists of row p to cand_*[cs * m + p][2 kC] and their thresholds to
 // thr_out[cs * m + p][2].  SAMP > 0: sampling pass over every SAMP-th tile
 // of a long slice first (threshold floor).
-template <int TN, int NP, bool STASH, int SAMP>
+template <int TN, int NP, int SAMP>
 __global__ void __launch_bounds__(kThreads, 1)
     screen_tc_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int m, int n,
-                     int ncs, const int* __restrict__ rows, int ksteps, int32_t* __restrict__ cand_idx,
+                     int ncs, const int* __restrict__ rows, int32_t* __restrict__ cand_idx,
                      float* __restrict__ cand_val, float* __restrict__ thr_out, int* __restrict__ status,
                      unsigned long long* __restrict__ tiles_run) {
-  using S = Screen<TN, NP, STASH>;
+  using S = Screen<TN, NP>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;                                  // [kPlanes][kATile]
   uint8_t* sB = sA + S::kPlanes * kATile;              // [kStages][kPlanes][kBTile]
-  float* lv = reinterpret_cast<float*>(sB + S::kStages * S::kPlanes * S::kBTile);
-  int* li = reinterpret_cast<int*>(lv + kC * kLists);
-  float* smv_all = reinterpret_cast<float*>(li + kC * kLists);        // [kNSub][kLists] sub-list minima
-  int* smp_all = reinterpret_cast<int*>(smv_all + kNSub * kLists);     // [kNSub][kLists] their slots
-  unsigned long long* pubs = reinterpret_cast<unsigned long long*>(smp_all + kNSub * kLists);  // [kLists] (tag, minimum)
-  uint32_t* stash = reinterpret_cast<uint32_t*>(pubs + kLists);       // [kEpiWarps * 32][kSlot] (STASH)
-  Bars* bs = reinterpret_cast<Bars*>(reinterpret_cast<uint8_t*>(stash) + S::kStash);
+  float* lv = reinterpret_cast<float*>(sB + S::kStages * S::kPlanes * S::kBTile);  // [kLists][kC]
+  int* li = reinterpret_cast<int*>(lv + kC * kLists);                              // [kLists][kC]
+  unsigned long long* pubs = reinterpret_cast<unsigned long long*>(li + kC * kLists);  // [kLists] (tag, minimum)
+  uint32_t* stage_all = reinterpret_cast<uint32_t*>(pubs + kLists);              // [kEpiWarps][32]
+  Bars* bs = reinterpret_cast<Bars*>(stage_all + kEpiWarps * 32);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S::kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
@@ -422,15 +294,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::fence_after_sync();
           const uint32_t bh = tc::smem_u32(sB + s * S::kPlanes * S::kBTile), bl = bh + S::kBTile;
           const uint32_t d = tmem + uint32_t(b * TN);
-          for (int ks = 0; ks < ksteps; ++ks) {
+#pragma unroll
+          for (int ks = 0; ks < kKP / 16; ++ks) {  // K = 64 always: the padding columns are exact zeros
             tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, ks > 0);
             if (NP == 3) {
               tc::mma_bf16(d, tc::sdesc_k128(ah + ks * 32), tc::sdesc_k128(bl + ks * 32), idesc, 1u);
               tc::mma_bf16(d, tc::sdesc_k128(al + ks * 32), tc::sdesc_k128(bh + ks * 32), idesc, 1u);
             }
           }
+          tc::mma_commit(&bs->accf[b]);  // the epilogue's hand-off first: it is on the critical chain
           tc::mma_commit(&bs->empty[s]);
-          tc::mma_commit(&bs->accf[b]);
         }
         tc::mma_commit(&bs->aempty);
       }
@@ -442,17 +315,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue ----------------
     const int ew = warp - 2;
-    const int half = ew >> 2;  // half of the tile's columns
+    const int half = ew >> 2;  // half of the tile's columns (warp-uniform)
     const int q = warp & 3;    // TMEM lane quarter this warp may access
     const int row_local = q * 32 + lane;
-    const int L = half * kTM + row_local;
-    float* mlv = lv + L;
-    int* mli = li + L;
-    float* msv = smv_all + L;
-    int* msp = smp_all + L;
+    const int Lw = half * kTM + q * 32;  // list of lane 0 of this warp
+    const int L = Lw + lane;
     unsigned long long* mine = pubs + L;
     const volatile unsigned long long* partner = pubs + (1 - half) * kTM + row_local;
-    uint32_t* slot = stash + (ew * 32 + lane) * kSlot;
+    uint32_t* stg = stage_all + ew * 32;
     long long accu = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x) {
       if (__any_sync(kFull, aborted(bs))) break;
@@ -462,9 +332,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int self = p < m ? (rows ? rows[p] : p) : -1;     // its column in Psi
       const int64_t out = int64_t(cs) * m + p;                 // its list pair
       const unsigned tag = unsigned(w);
-      ListState st{0, 0, -1.f};
-      bool parked = false;  // this lane's stash slot holds a chunk
-      int sj = 0;           // its first column
+#pragma unroll 4
+      for (int x = 0; x < 32; ++x) lv[(Lw + x) * kC + lane] = -1.f, li[(Lw + x) * kC + lane] = -1;  // the warp's lists
+      float minv = -1.f;  // this lane's list minimum (-1 until full)
       bool ok = true;
       const int ns = sample_tiles<SAMP>(t0, t1);
       float floor_v = -1.f;  // no floor until a sampling pass has run
@@ -474,12 +344,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int x = 0; x < kSampK; ++x) top[x] = -1.f;
         for (int u = 0; u < ns; ++u, ++accu) {
           uint32_t r[S::kChunks][32];
-          ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r);
+          float cm[S::kChunks];
+          ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r, cm);
           if (!ok) break;
           const int j0 = (t0 + u * SAMP) * TN + half * (TN / 2);
 #pragma unroll
           for (int c = 0; c < S::kChunks; ++c) {
-            float mx = chunk_absmax(r[c]);
+            float mx = cm[c];
             const int se = self - (j0 + c * 32);
             if (se >= 0 && se < 32) {  // the row's own column is no edge
               mx = 0.f;
@@ -496,41 +367,55 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         floor_v = top[kSampK - 1];
       }
+      __syncwarp();
+      float thr = fmaxf(floor_v, minv);
       for (int t = t0; ok && t < t1; ++t, ++accu) {
         uint32_t r[S::kChunks][32];
-        ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r);
+        float cm[S::kChunks];
+        ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r, cm);
         if (!ok) break;
-        const int j0 = t * TN + half * (TN / 2);
-        const float thr = fmaxf(floor_v, fmaxf(st.minv, partner_min(partner, tag)));
+        const int j0 = t * TN + half * (TN / 2);  // warp-uniform
+        thr = fmaxf(thr, partner_min(partner, tag));
 #pragma unroll
         for (int c = 0; c < S::kChunks; ++c) {
-          if (chunk_absmax(r[c]) > thr) {
-            if (STASH && !parked) {
+          // (the chunk holding a row's own column always passes: the insert drops that column)
+          unsigned hm = __ballot_sync(kFull, cm[c] > thr);
+          while (hm) {  // lanes whose chunk c beats their threshold, one at a time
+            const int h = __ffs(hm) - 1;
+            hm &= hm - 1;
+            if (lane == h) {
 #pragma unroll
               for (int k = 0; k < 8; ++k)
-                reinterpret_cast<uint4*>(slot)[k] = make_uint4(r[c][4 * k], r[c][4 * k + 1], r[c][4 * k + 2], r[c][4 * k + 3]);
-              parked = true;
-              sj = j0 + c * 32;
-            } else {
-              st = insert_chunk(r[c], j0 + c * 32, self, n, mlv, mli, msv, msp, mine, partner, tag, st, floor_v);
+                reinterpret_cast<uint4*>(stg)[k] =
+                    make_uint4(r[c][4 * k], r[c][4 * k + 1], r[c][4 * k + 2], r[c][4 * k + 3]);
+            }
+            __syncwarp();
+            const int j = j0 + c * 32 + lane;
+            const int self_h = __shfl_sync(kFull, self, h);  // (every lane takes part in each shuffle)
+            const float thr_h = __shfl_sync(kFull, thr, h);
+            const float x = (j < n && j != self_h) ? fabsf(__uint_as_float(stg[lane])) : -1.f;
+            const float mnew = coop_insert(lv, li, Lw + h, lane, x, j, thr_h);
+            __syncwarp();
+            if (lane == h) {
+              minv = mnew;
+              thr = fmaxf(thr, mnew);
+              *reinterpret_cast<volatile unsigned long long*>(mine) =
+                  (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(mnew);  // for the partner
             }
           }
         }
-        if (STASH && __popc(__ballot_sync(kFull, parked)) >= kBatch) {
-          if (parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st, floor_v);
-          parked = false;
-          __syncwarp();
-        }
       }
       if (!ok || __any_sync(kFull, aborted(bs))) break;
-      if (STASH && parked) st = drain(slot, sj, self, n, mlv, mli, msv, msp, mine, partner, tag, st, floor_v);
-      if (p < m) {
-        for (int c = 0; c < kC; ++c) {
-          cand_idx[out * (2 * kC) + half * kC + c] = c < st.cnt ? mli[c * kLists] : -1;
-          cand_val[out * (2 * kC) + half * kC + c] = c < st.cnt ? mlv[c * kLists] : -1.f;
+      __syncwarp();
+      for (int x = 0; x < 32; ++x) {  // the warp's lists, one coalesced row of kC slots each
+        const int px = rb * kTM + q * 32 + x;
+        if (px < m) {
+          const int64_t o = (int64_t(cs) * m + px) * (2 * kC) + half * kC + lane;
+          cand_idx[o] = li[(Lw + x) * kC + lane];
+          cand_val[o] = lv[(Lw + x) * kC + lane];
         }
-        thr_out[out * 2 + half] = fmaxf(floor_v, st.minv);  // -1: no floor and the list never full
       }
+      if (p < m) thr_out[out * 2 + half] = fmaxf(floor_v, minv);  // -1: no floor and the list never full
       __syncwarp();
     }
   }
@@ -613,7 +498,7 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int boxrows) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int TN, int NP, bool STASH, int SAMP>
+template <int TN, int NP, int SAMP>
 cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, const void* bh, const void* bl, int n,
                        int ncs, const int* rows, int r, int32_t* cidx, float* cval, float* thr,
                        unsigned long long* tiles_run = nullptr) {
@@ -622,21 +507,21 @@ cudaError_t run_screen(gmgm_handle* h, const void* ah, const void* al, int m, co
   mal = mah;
   mbl = mbh;
   if (NP == 3 && (!make_map(&mal, al, m, kTM) || !make_map(&mbl, bl, n, TN))) return cudaErrorInvalidValue;
-  auto kern = screen_tc_kernel<TN, NP, STASH, SAMP>;
-  const size_t smem = smem_bytes<Screen<TN, NP, STASH>>();
+  auto kern = screen_tc_kernel<TN, NP, SAMP>;
+  const size_t smem = smem_bytes<Screen<TN, NP>>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const int items = int((m + kTM - 1) / kTM) * ncs;
   const int grid = std::min(items, h->num_sms);
-  kern<<<grid, kThreads, smem, h->stream>>>(mah, mal, mbh, mbl, m, n, ncs, rows, (r + 15) / 16, cidx, cval, thr,
-                                            h->d_status, tiles_run);
+  kern<<<grid, kThreads, smem, h->stream>>>(mah, mal, mbh, mbl, m, n, ncs, rows, cidx, cval, thr, h->d_status,
+                                            tiles_run);
   return cudaGetLastError();
 }
 
 // main: TN 256, one product, stash, sampling pass over every 16th tile;
 // repair: TN 128, split products
-using MainScreen = Screen<256, 1, true>;
-using RepairScreen = Screen<128, 3, false>;
+using MainScreen = Screen<256, 1>;
+using RepairScreen = Screen<128, 3>;
 static_assert(smem_bytes<MainScreen>() <= kSmemCap && smem_bytes<RepairScreen>() <= kSmemCap, "shared memory");
 
 }  // namespace
@@ -669,7 +554,7 @@ cudaError_t launch_screen_tc(gmgm_handle* h, int64_t d, int r, const void* V, in
   }
   note_launch(2);
   // rows [row0, row0 + m): their A rows are contiguous from row row0
-  return run_screen<256, 1, true, 16>(h, A + row0 * kKP, nullptr, int(m), B, nullptr, int(d), 1, rows, r, cidx, cval,
+  return run_screen<256, 1, 16>(h, A + row0 * kKP, nullptr, int(m), B, nullptr, int(d), 1, rows, r, cidx, cval,
                                       thr, tiles_run);
 }
 
@@ -689,7 +574,7 @@ cudaError_t launch_screen_tc_repair(gmgm_handle* h, int64_t d, int r, const void
     prep_split_kernel<<<blocks, 256, 0, h->stream>>>(V, v64, ldv, psi, d, r, rows, m, Bh, Bl, Ah, Al);
   }
   note_launch(2);
-  return run_screen<128, 3, false, 0>(h, Ah, Al, m, Bh, Bl, int(d), ncs, rows, r, cidx, cval, thr);
+  return run_screen<128, 3, 0>(h, Ah, Al, m, Bh, Bl, int(d), ncs, rows, r, cidx, cval, thr);
 }
 
 }  // namespace gmgm
