@@ -9,22 +9,26 @@
 //                  main screen could not certify.
 // Persistent, warp-specialised, one CTA per SM:
 //   warp 0      TMA producer: the CTA's 128 A rows once per row block, then
-//               every B tile into a 3-stage shared-memory ring;
+//               every B tile into a shared-memory ring;
 //   warp 1      MMA issuer (one thread): per B tile D[128 x TN] = A B^T
 //               (K = 64 in four K=16 steps), FP32 in TMEM, double-buffered;
-//   warps 2-9   epilogue: two threads per row (one per half of the tile's
-//               columns), each owning a kC-slot candidate list; tcgen05.ld.red
-//               (sm_103a) brings 32 columns at a time together with their
-//               largest magnitude, so a chunk costs one compare against the
-//               list's threshold.
-// A chunk that beats its row's threshold is merged by the whole warp: the
-// owning lane stages its 32 values in shared memory, each lane takes one,
-// and the winners enter the row's list, which is kept sorted over the lanes
-// (lane c holds slot c; a ballot finds each winner's position and the lanes
-// below it shift down one slot).  The threshold of a (row, half) list is the
-// larger of its own minimum and its partner's (each list publishes its
-// minimum in shared memory once full); a stale read only admits more
-// candidates.
+//   warps 2-9   screening: two threads per row (one per half of the tile's
+//               columns); tcgen05.ld.red (sm_103a) brings 32 columns at a
+//               time together with their largest magnitude, so a chunk costs
+//               one compare against its row's threshold, and a chunk that
+//               beats it is copied (32 values) into the warp's queue in
+//               shared memory;
+//   warps 10-11 merging: each owns the (row, half) candidate lists of one
+//               half and takes up to 32 queued chunks at a time, one per
+//               lane, so 32 lists take their winners in parallel; it
+//               publishes each list's minimum, and the screening threads
+//               read their own and their partner's (the other half of the
+//               row) as their threshold.
+// The screening warps hand the accumulator back to the MMA right after
+// loading it, and a chunk with winners costs them one copy, not a merge:
+// the accumulator hand-off no longer waits on list updates, whose cost is
+// about the same for 1 or 32 chunks.  A stale threshold only lets more
+// chunks through.
 // Threshold floor (main screen, long sweeps): a sampling pass over every
 // 16th B tile first keeps, per (row, half), the 6 largest 32-column chunk
 // maxima in registers (a branch-free insert per chunk); the 6th of them is a
@@ -57,13 +61,29 @@ constexpr int kKP = 64;                      // padded K (bf16 elements, one 128
 constexpr int kMaxStages = 4;                // B-tile ring depth at most
 constexpr size_t kSmemCap = 232448;          // dynamic shared memory per CTA
 constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kInsWarps = 2;                 // list-merging warps, one per half of the tile's columns
+constexpr int kThreads = 64 + 32 * (kEpiWarps + kInsWarps);
+constexpr int kQ = 32;                       // queued hit chunks per epilogue warp (a power of two, >= 32)
+constexpr int kQStride = 36;                 // words per queued chunk (32 values, 16-byte aligned rows)
+constexpr int kQEnd = -1, kQDone = -2;       // queue entries that close a work item / the launch
 constexpr int kATile = kTM * kKP * 2;        // 16 KB per plane
 constexpr int kLists = 2 * kTM;              // (row, half) lists per CTA
 constexpr unsigned kFull = 0xffffffffu;
 constexpr long long kSpin = 1ll << 23;       // polls per bounded wait
 constexpr int kSampK = 6;                    // chunk maxima kept by the sampling pass
 constexpr int kSampMinTiles = 128;           // shortest slice that takes a sampling pass
+
+// Release store / acquire load of a shared-memory word (CTA scope): the
+// queue positions that hand hit chunks from the screening warps to the
+// merging warps.
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(tc::smem_u32(p)) : "memory");
+  return v;
+}
 
 // Sampling-pass tiles of the slice [t0, t1): every SAMP-th tile, when the
 // slice is long enough for a floor to pay.
@@ -100,8 +120,12 @@ struct Screen {
   static constexpr int kPlanes = NP == 3 ? 2 : 1;         // hi (+ lo)
   static constexpr int kBTile = TN * kKP * 2;             // per plane
   static constexpr int kTmemCols = 2 * TN;
-  // lists (values, columns), published minima, one 32-value staging row per epilogue warp
-  static constexpr size_t kLists_ = size_t(2) * kC * kLists * 4 + size_t(kLists) * 8 + size_t(kEpiWarps) * 32 * 4;
+  // lists (values, columns, slot-major), per list its count, minimum and
+  // the minimum's slot, the published minima, and per epilogue warp a queue
+  // of kQ hit chunks (values, (first column | lane) word, threshold) with its
+  // two positions
+  static constexpr size_t kLists_ = size_t(2) * kC * kLists * 4 + size_t(3) * kLists * 4 + size_t(kLists) * 8 +
+                                    size_t(kEpiWarps) * (size_t(kQ) * (kQStride + 2) * 4 + 2 * 4);
   static constexpr size_t kFixed = 1024 /*align slack*/ + size_t(kPlanes) * kATile + kLists_ + sizeof(Bars);
   static constexpr int kStages = int((kSmemCap - kFixed) / (size_t(kPlanes) * kBTile)) < kMaxStages
                                      ? int((kSmemCap - kFixed) / (size_t(kPlanes) * kBTile))
@@ -121,38 +145,35 @@ __device__ __forceinline__ void raise_abort(Bars* bs, int* status) {
 
 __device__ __forceinline__ bool aborted(Bars* bs) { return *reinterpret_cast<volatile int*>(&bs->abort) != 0; }
 
-__device__ __forceinline__ float partner_min(const volatile unsigned long long* partner, unsigned tag) {
-  const unsigned long long pv = *partner;
+// A list's published minimum for work item `tag` (-1 while it is not full or
+// still shows an earlier item).
+__device__ __forceinline__ float list_min(const volatile unsigned long long* pub, unsigned tag) {
+  const unsigned long long pv = *pub;
   return unsigned(pv >> 32) == tag ? __uint_as_float(unsigned(pv)) : -1.f;
 }
 
-// Warp-cooperative insert into one (row, half) list.  The list is sorted in
-// descending order over the lanes: lane c holds slot c (value lv[Lr * kC +
-// c], column li[...]), empty slots hold -1, so slot 31 is the list's minimum
-// once it is full and -1 before.  Every lane offers at most one magnitude x
-// (column jx; -1 offers nothing); those above `thr` are inserted one by one
-// in lane order (a ballot finds the insertion position, the lanes below it
-// shift down one slot and the last slot falls out).  Returns the new
-// minimum.  Called by the whole warp.
-__device__ __forceinline__ float coop_insert(float* lv, int* li, int Lr, int lane, float x, int jx, float thr) {
-  float lval = lv[Lr * kC + lane];
-  int lidx = li[Lr * kC + lane];
-  unsigned w = __ballot_sync(kFull, x > thr);
-  while (w) {
-    const int e = __ffs(w) - 1;
-    w &= w - 1;
-    const float v = __shfl_sync(kFull, x, e);
-    const int j = __shfl_sync(kFull, jx, e);
-    if (v <= __shfl_sync(kFull, lval, 31)) continue;  // below the list's minimum by now (warp-uniform)
-    const int pos = __popc(__ballot_sync(kFull, lval >= v));
-    const float uv = __shfl_up_sync(kFull, lval, 1);
-    const int ui = __shfl_up_sync(kFull, lidx, 1);
-    if (lane > pos) lval = uv, lidx = ui;
-    if (lane == pos) lval = v, lidx = j;
+// One (row, half) list, slot-major (slot c of list L at [c * kLists + L]),
+// unsorted: it fills, then an offer above its minimum replaces the minimum
+// and a rescan of the 32 slots finds the next.  `cnt`, `minv` and `minp`
+// live in shared memory between offers.  One lane per list.
+__device__ __forceinline__ void list_offer(float* lv, int* li, int L, int& cnt, float& minv, int& minp, float v,
+                                           int j) {
+  if (cnt < kC) {
+    lv[cnt * kLists + L] = v;
+    li[cnt * kLists + L] = j;
+    if (++cnt < kC) return;
+  } else {
+    if (v <= minv) return;
+    lv[minp * kLists + L] = v;
+    li[minp * kLists + L] = j;
   }
-  lv[Lr * kC + lane] = lval;
-  li[Lr * kC + lane] = lidx;
-  return __shfl_sync(kFull, lval, 31);
+  minv = lv[L];
+  minp = 0;
+#pragma unroll 8
+  for (int c = 1; c < kC; ++c) {
+    const float x = lv[c * kLists + L];
+    if (x < minv) minv = x, minp = c;
+  }
 }
 
 // Epilogue warp: wait for accumulator buffer accu & 1, pull this warp's lane
@@ -198,11 +219,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;                                  // [kPlanes][kATile]
   uint8_t* sB = sA + S::kPlanes * kATile;              // [kStages][kPlanes][kBTile]
-  float* lv = reinterpret_cast<float*>(sB + S::kStages * S::kPlanes * S::kBTile);  // [kLists][kC]
-  int* li = reinterpret_cast<int*>(lv + kC * kLists);                              // [kLists][kC]
-  unsigned long long* pubs = reinterpret_cast<unsigned long long*>(li + kC * kLists);  // [kLists] (tag, minimum)
-  uint32_t* stage_all = reinterpret_cast<uint32_t*>(pubs + kLists);              // [kEpiWarps][32]
-  Bars* bs = reinterpret_cast<Bars*>(stage_all + kEpiWarps * 32);
+  float* lv = reinterpret_cast<float*>(sB + S::kStages * S::kPlanes * S::kBTile);  // [kC][kLists]
+  int* li = reinterpret_cast<int*>(lv + kC * kLists);                              // [kC][kLists]
+  int* lcnt = reinterpret_cast<int*>(li + kC * kLists);                           // [kLists]
+  float* lmin = reinterpret_cast<float*>(lcnt + kLists);                          // [kLists]
+  int* lminp = reinterpret_cast<int*>(lmin + kLists);                             // [kLists]
+  unsigned long long* pubs = reinterpret_cast<unsigned long long*>(lminp + kLists);  // [kLists] (tag, minimum)
+  uint32_t* qval_all = reinterpret_cast<uint32_t*>(pubs + kLists);               // [kEpiWarps][kQ][kQStride]
+  int* qmeta_all = reinterpret_cast<int*>(qval_all + kEpiWarps * kQ * kQStride); // [kEpiWarps][kQ]
+  float* qthr_all = reinterpret_cast<float*>(qmeta_all + kEpiWarps * kQ);        // [kEpiWarps][kQ]
+  int* qpos = reinterpret_cast<int*>(qthr_all + kEpiWarps * kQ);                 // [kEpiWarps][2]: tail, head
+  Bars* bs = reinterpret_cast<Bars*>(qpos + kEpiWarps * 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S::kStages; ++s) tc::mbar_init(&bs->full[s], 1), tc::mbar_init(&bs->empty[s], 1);
@@ -221,7 +248,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::prefetch_tmap(&tmBl);
     }
   }
-  for (int L = threadIdx.x; L < kLists; L += blockDim.x) pubs[L] = ~0ull;  // no row block yet
+  for (int L = threadIdx.x; L < kLists; L += blockDim.x)
+    pubs[L] = ~0ull, lcnt[L] = 0, lmin[L] = -1.f, lminp[L] = 0;  // empty lists, no row block yet
+  for (int x = threadIdx.x; x < kEpiWarps * 2; x += blockDim.x) qpos[x] = 0;
   if (warp == 1) tc::tmem_alloc(&bs->tmem_base, S::kTmemCols);
   __syncthreads();
   tc::fence_after_sync();
@@ -312,33 +341,53 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_wait(&bs->done, 0, kSpin);
       if (tiles_run) atomicAdd(tiles_run, static_cast<unsigned long long>(used));
     }
-  } else {
+  } else if (warp < 2 + kEpiWarps) {
     // ---------------- epilogue ----------------
+    // Screens each tile's chunks against the row's threshold and queues the
+    // chunks that beat it for the merging warp of its half.
     const int ew = warp - 2;
     const int half = ew >> 2;  // half of the tile's columns (warp-uniform)
     const int q = warp & 3;    // TMEM lane quarter this warp may access
     const int row_local = q * 32 + lane;
-    const int Lw = half * kTM + q * 32;  // list of lane 0 of this warp
-    const int L = Lw + lane;
-    unsigned long long* mine = pubs + L;
+    const int L = half * kTM + row_local;
+    const volatile unsigned long long* own = pubs + L;
     const volatile unsigned long long* partner = pubs + (1 - half) * kTM + row_local;
-    uint32_t* stg = stage_all + ew * 32;
+    uint32_t* qval = qval_all + ew * kQ * kQStride;
+    int* qmeta = qmeta_all + ew * kQ;
+    float* qthr = qthr_all + ew * kQ;
+    int* qtail = qpos + ew * 2;
+    const int* qhead = qpos + ew * 2 + 1;
+    const unsigned lt = (1u << lane) - 1u;
+    int tail = 0, head_seen = 0;
+    bool ok = true;
+    // room for `need` more entries; false (abort raised) when the wait gives up
+    auto room = [&](int need) -> bool {
+      if (tail + need - head_seen <= kQ) return true;
+      const uint64_t t0 = tc::globaltimer_ns();
+      for (;;) {
+        head_seen = __shfl_sync(kFull, lane == 0 ? ld_acquire(qhead) : 0, 0);
+        if (tail + need - head_seen <= kQ) return true;
+        if (__any_sync(kFull, aborted(bs)) || tc::globaltimer_ns() - t0 > tc::kWaitLimitNs) {
+          if (lane == 0) raise_abort(bs, status);
+          return false;
+        }
+      }
+    };
+    auto publish = [&]() {  // the entries written so far become visible to the merging warp
+      __syncwarp();
+      if (lane == 0) st_release(qtail, tail);
+    };
     long long accu = 0;
-    for (int w = blockIdx.x; w < items; w += gridDim.x) {
+    for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
       if (__any_sync(kFull, aborted(bs))) break;
-      const int rb = w / ncs, cs = w - rb * ncs;
+      const int cs = w % ncs;
       const int t0 = cs * per_slice, t1 = min(ntiles, t0 + per_slice);
-      const int p = rb * kTM + row_local;                      // row of A
-      const int self = p < m ? (rows ? rows[p] : p) : -1;     // its column in Psi
-      const int64_t out = int64_t(cs) * m + p;                 // its list pair
       const unsigned tag = unsigned(w);
-#pragma unroll 4
-      for (int x = 0; x < 32; ++x) lv[(Lw + x) * kC + lane] = -1.f, li[(Lw + x) * kC + lane] = -1;  // the warp's lists
-      float minv = -1.f;  // this lane's list minimum (-1 until full)
-      bool ok = true;
       const int ns = sample_tiles<SAMP>(t0, t1);
       float floor_v = -1.f;  // no floor until a sampling pass has run
       if (SAMP > 0 && ns > 0) {
+        const int p = (w / ncs) * kTM + row_local;
+        const int self = p < m ? (rows ? rows[p] : p) : -1;  // its column in Psi
         float top[kSampK];   // largest chunk maxima so far, descending
 #pragma unroll
         for (int x = 0; x < kSampK; ++x) top[x] = -1.f;
@@ -367,56 +416,200 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         floor_v = top[kSampK - 1];
       }
-      __syncwarp();
-      float thr = fmaxf(floor_v, minv);
+      float thr = floor_v;
       for (int t = t0; ok && t < t1; ++t, ++accu) {
         uint32_t r[S::kChunks][32];
         float cm[S::kChunks];
         ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r, cm);
         if (!ok) break;
         const int j0 = t * TN + half * (TN / 2);  // warp-uniform
-        thr = fmaxf(thr, partner_min(partner, tag));
+        thr = fmaxf(thr, fmaxf(list_min(own, tag), list_min(partner, tag)));
 #pragma unroll
         for (int c = 0; c < S::kChunks; ++c) {
-          // (the chunk holding a row's own column always passes: the insert drops that column)
-          unsigned hm = __ballot_sync(kFull, cm[c] > thr);
-          while (hm) {  // lanes whose chunk c beats their threshold, one at a time
-            const int h = __ffs(hm) - 1;
-            hm &= hm - 1;
-            if (lane == h) {
+          // (the chunk holding a row's own column always passes: the merge drops that column)
+          const bool hit = cm[c] > thr;
+          const unsigned hm = __ballot_sync(kFull, hit);
+          if (hm) {
+            const int cnt = __popc(hm);
+            if (!room(cnt)) {
+              ok = false;
+              break;
+            }
+            if (hit) {
+              const int slot = (tail + __popc(hm & lt)) & (kQ - 1);
+              uint4* dst = reinterpret_cast<uint4*>(qval + slot * kQStride);
 #pragma unroll
               for (int k = 0; k < 8; ++k)
-                reinterpret_cast<uint4*>(stg)[k] =
-                    make_uint4(r[c][4 * k], r[c][4 * k + 1], r[c][4 * k + 2], r[c][4 * k + 3]);
+                dst[k] = make_uint4(r[c][4 * k], r[c][4 * k + 1], r[c][4 * k + 2], r[c][4 * k + 3]);
+              qmeta[slot] = (j0 + c * 32) | lane;
+              qthr[slot] = thr;
             }
-            __syncwarp();
-            const int j = j0 + c * 32 + lane;
-            const int self_h = __shfl_sync(kFull, self, h);  // (every lane takes part in each shuffle)
-            const float thr_h = __shfl_sync(kFull, thr, h);
-            const float x = (j < n && j != self_h) ? fabsf(__uint_as_float(stg[lane])) : -1.f;
-            const float mnew = coop_insert(lv, li, Lw + h, lane, x, j, thr_h);
-            __syncwarp();
-            if (lane == h) {
-              minv = mnew;
-              thr = fmaxf(thr, mnew);
-              *reinterpret_cast<volatile unsigned long long*>(mine) =
-                  (static_cast<unsigned long long>(tag) << 32) | __float_as_uint(mnew);  // for the partner
-            }
+            tail += cnt;
+            publish();
           }
         }
       }
-      if (!ok || __any_sync(kFull, aborted(bs))) break;
+      if (!ok || !room(1)) break;
+      // close the item: the rows' floors travel in the entry's values
+      const int slot = tail & (kQ - 1);
+      qval[slot * kQStride + lane] = __float_as_uint(floor_v);
+      if (lane == 0) qmeta[slot] = kQEnd;
+      ++tail;
+      publish();
+    }
+    if (room(1)) {  // no more items (or an abort): release the merging warp
+      if (lane == 0) qmeta[tail & (kQ - 1)] = kQDone;
+      ++tail;
+      publish();
+    }
+  } else {
+    // ---------------- list merging ----------------
+    // Warp iw owns the lists of half iw, fed by the queues of epilogue warps
+    // 4 iw .. 4 iw + 3.  It takes up to 32 queued chunks at a time, one per
+    // lane, and each lane merges its chunk's winners into its row's list
+    // (lanes whose chunks share a list take turns), then publishes the list's
+    // minimum for the screen.  A queue's closing entry writes its 32 lists out
+    // with their thresholds and empties them for the next work item.
+    const int iw = warp - 2 - kEpiWarps;
+    const unsigned lt = (1u << lane) - 1u;
+    int head[4] = {0, 0, 0, 0}, item_no[4] = {0, 0, 0, 0};
+    unsigned done_mask = 0;
+    uint64_t idle_since = 0;
+    int patience = 0;
+    while (done_mask != 0xFu) {
+      // -- gather: entries available in the four queues, up to each queue's next closing entry
+      int avail[4];
+      int total = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ew = iw * 4 + k;
+        const int tl = (done_mask >> k) & 1u ? head[k] : __shfl_sync(kFull, lane == 0 ? ld_acquire(qpos + ew * 2) : 0, 0);
+        avail[k] = tl - head[k];
+      }
       __syncwarp();
-      for (int x = 0; x < 32; ++x) {  // the warp's lists, one coalesced row of kC slots each
-        const int px = rb * kTM + q * 32 + x;
-        if (px < m) {
-          const int64_t o = (int64_t(cs) * m + px) * (2 * kC) + half * kC + lane;
-          cand_idx[o] = li[(Lw + x) * kC + lane];
-          cand_val[o] = lv[(Lw + x) * kC + lane];
+      // lane i takes the i-th available entry (queues in order); closing entries stop their queue's run
+      int my_k = -1, my_pos = 0;
+      {
+        int before = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int ew = iw * 4 + k;
+          // first closing entry among this queue's available ones (lanes look at one each)
+          const bool look = lane < avail[k];
+          const int meta = look ? qmeta_all[ew * kQ + ((head[k] + lane) & (kQ - 1))] : 0;
+          const unsigned closing = __ballot_sync(kFull, look && meta < 0);
+          const int run = closing ? __ffs(closing) - 1 : avail[k];  // ordinary entries before it
+          const int take = min(run, 32 - before);                    // those that still find a lane
+          if (lane >= before && lane < before + take) my_k = k, my_pos = head[k] + (lane - before);
+          avail[k] = closing && take == run ? -(take + 1) : take;  // negative: the closing entry is next
+          before += take;
+        }
+        total = before;
+      }
+      // a short wait lets a batch grow (the merge costs about the same for 1 or 32 chunks)
+      bool closing_any = false;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) closing_any |= avail[k] < 0;
+      if (total < 8 && !closing_any && patience < 8) {
+        ++patience;
+        __nanosleep(256);
+        continue;
+      }
+      patience = 0;
+      bool progress = total > 0;
+      // -- merge: one chunk per lane
+      if (my_k >= 0) {
+        const int ew = iw * 4 + my_k;
+        const int slot = my_pos & (kQ - 1);
+        const int meta = qmeta_all[ew * kQ + slot];
+        const float thr_e = qthr_all[ew * kQ + slot];
+        const uint32_t* vals = qval_all + (ew * kQ + slot) * kQStride;
+        const int h = meta & 31;
+        const int jc = meta & ~31;
+        const int qw = (ew + 2) & 3;
+        const int Lm = iw * kTM + qw * 32 + h;
+        const int w = blockIdx.x + item_no[my_k] * gridDim.x;
+        const int p = (w / ncs) * kTM + qw * 32 + h;
+        const int self = p < m ? (rows ? rows[p] : p) : -1;
+        unsigned win = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint4 v4 = reinterpret_cast<const uint4*>(vals)[k];
+          win |= (fabsf(__uint_as_float(v4.x)) > thr_e ? 1u : 0u) << (4 * k);
+          win |= (fabsf(__uint_as_float(v4.y)) > thr_e ? 1u : 0u) << (4 * k + 1);
+          win |= (fabsf(__uint_as_float(v4.z)) > thr_e ? 1u : 0u) << (4 * k + 2);
+          win |= (fabsf(__uint_as_float(v4.w)) > thr_e ? 1u : 0u) << (4 * k + 3);
+        }
+        if (self - jc >= 0 && self - jc < 32) win &= ~(1u << (self - jc));
+        if (n - jc < 32) win &= n - jc <= 0 ? 0u : (1u << (n - jc)) - 1u;
+        // lanes whose chunks share a list take turns, in lane order
+        const unsigned active = __activemask();
+        const unsigned peers = __match_any_sync(active, Lm);
+        const int turn = __popc(peers & lt);
+        const int turns = __popc(peers);
+        for (int tr = 0; tr < 32; ++tr) {
+          if (tr == turn) {
+            int cnt = lcnt[Lm], minp = lminp[Lm];
+            float minv = lmin[Lm];
+            while (win) {
+              const int e = __ffs(win) - 1;
+              win &= win - 1;
+              list_offer(lv, li, Lm, cnt, minv, minp, fabsf(__uint_as_float(vals[e])), jc + e);
+            }
+            lcnt[Lm] = cnt, lmin[Lm] = minv, lminp[Lm] = minp;
+            *reinterpret_cast<volatile unsigned long long*>(pubs + Lm) =
+                (static_cast<unsigned long long>(unsigned(w)) << 32) | __float_as_uint(cnt < kC ? -1.f : minv);
+          }
+          if (__all_sync(active, tr + 1 >= turns)) break;
+          __syncwarp(active);
         }
       }
-      if (p < m) thr_out[out * 2 + half] = fmaxf(floor_v, minv);  // -1: no floor and the list never full
       __syncwarp();
+      // -- release the merged entries; then a closing entry at the head of a queue
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ew = iw * 4 + k;
+        const int run = avail[k] < 0 ? -avail[k] - 1 : avail[k];
+        head[k] += run;
+        if (avail[k] < 0) {
+          const int slot = head[k] & (kQ - 1);
+          const int meta = qmeta_all[ew * kQ + slot];
+          if (meta == kQEnd) {
+            const int qw = (ew + 2) & 3;
+            const int Lx = iw * kTM + qw * 32 + lane;  // lane x: list of row x of that quarter
+            const int w = blockIdx.x + item_no[k] * gridDim.x;
+            const int rb = w / ncs, cs = w - rb * ncs;
+            const int px = rb * kTM + qw * 32 + lane;
+            const float floor_x = __uint_as_float(qval_all[(ew * kQ + slot) * kQStride + lane]);
+            const int cnt = lcnt[Lx];
+            if (px < m) {
+              const int64_t o = (int64_t(cs) * m + px) * (2 * kC) + iw * kC;
+              for (int c = 0; c < kC; ++c) {
+                cand_idx[o + c] = c < cnt ? li[c * kLists + Lx] : -1;
+                cand_val[o + c] = c < cnt ? lv[c * kLists + Lx] : -1.f;
+              }
+              // every column left out has a screened value <= this (-1: no floor, list never full)
+              thr_out[(int64_t(cs) * m + px) * 2 + iw] = fmaxf(floor_x, cnt < kC ? -1.f : lmin[Lx]);
+            }
+            lcnt[Lx] = 0, lmin[Lx] = -1.f, lminp[Lx] = 0;
+            ++item_no[k];
+          } else {
+            done_mask |= 1u << k;
+          }
+          ++head[k];
+          progress = true;
+        }
+        __syncwarp();
+        if (lane == 0) st_release(qpos + ew * 2 + 1, head[k]);  // the slots are free again
+      }
+      if (progress) {
+        idle_since = 0;
+      } else {  // nothing queued: leave the issue slots to the epilogue warps for a while
+        const uint64_t now = tc::globaltimer_ns();
+        if (idle_since == 0) idle_since = now;
+        if (__any_sync(kFull, aborted(bs)) || now - idle_since > tc::kWaitLimitNs) break;
+        __nanosleep(200);
+      }
     }
   }
   __syncthreads();
