@@ -358,11 +358,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     int* qtail = qpos + ew * 2;
     const int* qhead = qpos + ew * 2 + 1;
     const unsigned lt = (1u << lane) - 1u;
-    int tail = 0, head_seen = 0;
+    int tail = 0, head_seen = 0, published = 0;
     bool ok = true;
+    auto publish = [&]() {  // the entries written so far become visible to the merging warp
+      __syncwarp();
+      if (lane == 0) st_release(qtail, tail);
+      published = tail;
+    };
     // room for `need` more entries; false (abort raised) when the wait gives up
     auto room = [&](int need) -> bool {
       if (tail + need - head_seen <= kQ) return true;
+      if (published != tail) publish();
       const uint64_t t0 = tc::globaltimer_ns();
       for (;;) {
         head_seen = __shfl_sync(kFull, lane == 0 ? ld_acquire(qhead) : 0, 0);
@@ -372,10 +378,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           return false;
         }
       }
-    };
-    auto publish = [&]() {  // the entries written so far become visible to the merging warp
-      __syncwarp();
-      if (lane == 0) st_release(qtail, tail);
     };
     long long accu = 0;
     for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
@@ -422,6 +424,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         float cm[S::kChunks];
         ok = take_tile<S>(bs, tmem, q, half, accu, lane, status, r, cm);
         if (!ok) break;
+        // the previous tile's chunks are published only now, once this tile's
+        // accumulator is back with the MMA (off the hand-off's critical path)
+        if (published != tail) publish();
         const int j0 = t * TN + half * (TN / 2);  // warp-uniform
         thr = fmaxf(thr, fmaxf(list_min(own, tag), list_min(partner, tag)));
 #pragma unroll
@@ -445,7 +450,6 @@ __global__ void __launch_bounds__(kThreads, 1)
               qthr[slot] = thr;
             }
             tail += cnt;
-            publish();
           }
         }
       }
@@ -480,13 +484,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       // -- gather: entries available in the four queues, up to each queue's next closing entry
       int avail[4];
       int total = 0;
+      {
+        const int my_tail = lane < 4 ? ld_acquire(qpos + (iw * 4 + lane) * 2) : 0;  // lanes 0-3: one queue each
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int ew = iw * 4 + k;
-        const int tl = (done_mask >> k) & 1u ? head[k] : __shfl_sync(kFull, lane == 0 ? ld_acquire(qpos + ew * 2) : 0, 0);
-        avail[k] = tl - head[k];
+        for (int k = 0; k < 4; ++k) {
+          const int tl = __shfl_sync(kFull, my_tail, k);
+          avail[k] = (done_mask >> k) & 1u ? 0 : tl - head[k];
+        }
       }
-      __syncwarp();
       // lane i takes the i-th available entry (queues in order); closing entries stop their queue's run
       int my_k = -1, my_pos = 0;
       {
@@ -528,7 +533,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int jc = meta & ~31;
         const int qw = (ew + 2) & 3;
         const int Lm = iw * kTM + qw * 32 + h;
-        const int w = blockIdx.x + item_no[my_k] * gridDim.x;
+        const int ino = my_k == 0 ? item_no[0] : my_k == 1 ? item_no[1] : my_k == 2 ? item_no[2] : item_no[3];
+        const int w = blockIdx.x + ino * gridDim.x;
         const int p = (w / ncs) * kTM + qw * 32 + h;
         const int self = p < m ? (rows ? rows[p] : p) : -1;
         unsigned win = 0;
@@ -547,7 +553,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned peers = __match_any_sync(active, Lm);
         const int turn = __popc(peers & lt);
         const int turns = __popc(peers);
-        for (int tr = 0; tr < 32; ++tr) {
+        const int rounds = __reduce_max_sync(active, unsigned(turns));
+        for (int tr = 0; tr < rounds; ++tr) {
           if (tr == turn) {
             int cnt = lcnt[Lm], minp = lminp[Lm];
             float minv = lmin[Lm];
@@ -560,7 +567,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<volatile unsigned long long*>(pubs + Lm) =
                 (static_cast<unsigned long long>(unsigned(w)) << 32) | __float_as_uint(cnt < kC ? -1.f : minv);
           }
-          if (__all_sync(active, tr + 1 >= turns)) break;
           __syncwarp(active);
         }
       }
@@ -599,9 +605,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++head[k];
           progress = true;
         }
-        __syncwarp();
-        if (lane == 0) st_release(qpos + ew * 2 + 1, head[k]);  // the slots are free again
       }
+      __syncwarp();
+      if (lane < 4)  // the slots are free again (lanes 0-3: one queue each)
+        st_release(qpos + (iw * 4 + lane) * 2 + 1, lane == 0 ? head[0] : lane == 1 ? head[1] : lane == 2 ? head[2] : head[3]);
       if (progress) {
         idle_since = 0;
       } else {  // nothing queued: leave the issue slots to the epilogue warps for a while
