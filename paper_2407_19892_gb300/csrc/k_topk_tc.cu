@@ -428,7 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // accumulator is back with the MMA (off the hand-off's critical path)
         if (published != tail) publish();
         const int j0 = t * TN + half * (TN / 2);  // warp-uniform
-        thr = fmaxf(thr, fmaxf(list_min(own, tag), list_min(partner, tag)));
+        if ((t & 7) == 0)  // the lists' minima move slowly: every 8th tile is often enough
+          thr = fmaxf(thr, fmaxf(list_min(own, tag), list_min(partner, tag)));
 #pragma unroll
         for (int c = 0; c < S::kChunks; ++c) {
           // (the chunk holding a row's own column always passes: the merge drops that column)
