@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // accumulator is back with the MMA (off the hand-off's critical path)
         if (published != tail) publish();
         const int j0 = t * TN + half * (TN / 2);  // warp-uniform
-        if ((t & 7) == 0)  // the lists' minima move slowly: every 8th tile is often enough
+        if ((t & 31) == 0)  // the lists' minima move slowly: every 32nd tile is often enough
           thr = fmaxf(thr, fmaxf(list_min(own, tag), list_min(partner, tag)));
 #pragma unroll
         for (int c = 0; c < S::kChunks; ++c) {
