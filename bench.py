@@ -447,25 +447,26 @@ def main():
     from paper_2407_19892_gb300 import warmstart
     warm = None if a.no_warm_start else warmstart.load(dev)
 
+    # with the BF16 planes the FP32 X is never read (the Gram and the lift use the planes): not written
     def step(src):
-        x, hi, lo, ld_t = g.preprocess(src, split=split, h=h)
+        x, hi, lo, ld_t = g.preprocess(src, split=split, x_out=not split, h=h)
         return g.fit_two_axis(x, a.r_cells, a.genes, a.k_cells, a.k_genes, gram_prec=gram_prec,
                               topk_prec=topk_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, tol=a.tol,
-                              warm_params=warm, h=h)
+                              warm_params=warm, rows=a.cells, h=h)
 
     def staged_step(src):
         """The same step, stage by stage, with events between stages (untimed)."""
         names = ["preprocess", "gram", "eig", "lift", "solve", "topk_cells", "topk_genes"]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         ev[0].record(stream)
-        x, hi, lo, ld_t = g.preprocess(src, split=split, h=h)
+        x, hi, lo, ld_t = g.preprocess(src, split=split, x_out=not split, h=h)
         ev[1].record(stream)
-        S = g.gram(x, g.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
+        S = g.gram(x, g.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, rows=a.cells, cols=a.genes, h=h)
         ev[2].record(stream)
         e_all, W = g.spectra(S, a.genes, rv=a.r_cells, h=h)
         ev[3].record(stream)
         U = g.lift(x, W[:, :a.r_cells].contiguous(), e_all[:a.r_cells].contiguous(), a.r_cells, xt_hi=hi,
-                   xt_lo=lo, ld_t=ld_t, h=h)
+                   xt_lo=lo, ld_t=ld_t, rows=a.cells, h=h)
         ev[4].record(stream)
         e_c = e_all[:a.r_cells].contiguous()
         init = list(warmstart.infer(warm, e_c, e_all, h=h)) if warm is not None else None

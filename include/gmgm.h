@@ -139,7 +139,9 @@ uint64_t gmgm_kernel_launches(void);
 /* X = log1p(counts) - column means, for an n x p count matrix (cells x genes).
  *   counts  device, n x p FP32, leading dimension ldc >= p.
  *   x_out   device, n x p FP32, leading dimension ldx >= p; may alias counts
- *           (then ldx must equal ldc).
+ *           (then ldx must equal ldc).  May be NULL when xt_hi, xt_lo are
+ *           given: only the BF16 planes are written (the tensor-core Gram and
+ *           lift read nothing else), saving the n p FP32 stores.
  *   xt_hi, xt_lo  device, optional (both NULL or both set): the BF16 split of
  *           X^T, p x ld_t row-major (gene-major), hi = bf16(x),
  *           lo = bf16(x - hi); columns n..ld_t-1 are written as zero.

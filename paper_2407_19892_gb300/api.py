@@ -93,24 +93,28 @@ def _need_cuda(t, dtype, name):
 
 # ---- preprocessing ----------------------------------------------------------
 
-def preprocess(counts: torch.Tensor, split: bool = True, inplace: bool = False, h: Handle = None):
+def preprocess(counts: torch.Tensor, split: bool = True, inplace: bool = False, x_out: bool = True,
+               h: Handle = None):
     """log1p + column centring of an n x p FP32 count matrix on the GPU.
     Returns (X, xt_hi, xt_lo, ld_t); xt_* are p x ld_t BF16 planes of X^T
-    (None when split=False)."""
+    (None when split=False).  With split and x_out=False only the planes are
+    written and X is None (the tensor-core Gram and lift read nothing else)."""
     h = h or handle(counts.device)
     _need_cuda(counts, torch.float32, "counts")
     if counts.dim() != 2 or counts.stride(1) != 1:
         raise ValueError("counts must be a row-major 2-D tensor")
+    if not x_out and not split:
+        raise ValueError("x_out=False needs split=True")
     n, p = counts.shape
-    x = counts if inplace else torch.empty_like(counts)
+    x = None if not x_out else (counts if inplace else torch.empty_like(counts))
     hi = lo = None
     ld_t = 0
     if split:
         ld_t = ((n + 63) // 64) * 64
         hi = torch.empty(p, ld_t, dtype=torch.bfloat16, device=counts.device)
         lo = torch.empty(p, ld_t, dtype=torch.bfloat16, device=counts.device)
-    h.check(h.lib.gmgm_preprocess(h.h, n, p, _ptr(counts), counts.stride(0), _ptr(x), x.stride(0),
-                                  _ptr(hi), _ptr(lo), ld_t, None))
+    h.check(h.lib.gmgm_preprocess(h.h, n, p, _ptr(counts), counts.stride(0), _ptr(x),
+                                  x.stride(0) if x is not None else p, _ptr(hi), _ptr(lo), ld_t, None))
     return x, hi, lo, ld_t
 
 
@@ -484,19 +488,21 @@ def fit_multimodal(counts, r_cells: int, ks, gram_prec: int = L.BF16X3, topk_pre
         if c.dim() != 2 or c.shape[0] != n or c.stride(1) != 1:
             raise ValueError("every count matrix must be row-major cells x features with the same cells")
     split = gram_prec != L.FP32
-    x = torch.empty(n, P, dtype=torch.float32, device=dev)
+    # with the BF16 planes (and r_cells <= 64, the tensor-core lift) the FP32 X is never read: not written
+    x = None if split and r_cells <= 64 else torch.empty(n, P, dtype=torch.float32, device=dev)
     ld_t = ((n + 63) // 64) * 64 if split else 0
     hi = torch.empty(P, ld_t, dtype=torch.bfloat16, device=dev) if split else None
     lo = torch.empty(P, ld_t, dtype=torch.bfloat16, device=dev) if split else None
     off = 0
     for c, p in zip(counts, ps):
-        h.check(h.lib.gmgm_preprocess(h.h, n, p, _ptr(c), c.stride(0), _ptr(x[:, off:]), x.stride(0),
+        h.check(h.lib.gmgm_preprocess(h.h, n, p, _ptr(c), c.stride(0), _ptr(x[:, off:]) if x is not None else None,
+                                      x.stride(0) if x is not None else p,
                                       _ptr(hi[off:]) if split else None, _ptr(lo[off:]) if split else None,
                                       ld_t, None))
         off += p
-    S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)
+    S = gram(x, L.SIDE_COLS, gram_prec, xt_hi=hi, xt_lo=lo, ld_t=ld_t, rows=n, cols=P, h=h)
     e_c, W_c = spectra(S, r_cells, True, h=h)
-    E, V, Ss = [e_c], [lift(x, W_c, e_c, r_cells, xt_hi=hi, xt_lo=lo, ld_t=ld_t, h=h)], [S]
+    E, V, Ss = [e_c], [lift(x, W_c, e_c, r_cells, xt_hi=hi, xt_lo=lo, ld_t=ld_t, rows=n, h=h)], [S]
     off = 0
     for p in ps:
         Sb = S[off:off + p, off:off + p]

@@ -149,8 +149,8 @@ int gmgm_preprocess(gmgm_handle* h, int64_t n, int64_t p, const float* counts, i
                     float* x_out, int64_t ldx, uint16_t* xt_hi, uint16_t* xt_lo, int64_t ld_t,
                     double* colmean_out) {
   if (!h) return GMGM_E_ARG;
-  if (n < 2 || p < 1 || !counts || !x_out || ldc < p || ldx < p)
-    return fail(h, GMGM_E_ARG, "gmgm_preprocess: need n >= 2, p >= 1, ldc, ldx >= p, non-null buffers");
+  if (n < 2 || p < 1 || !counts || (!x_out && !xt_hi) || ldc < p || (x_out && ldx < p))
+    return fail(h, GMGM_E_ARG, "gmgm_preprocess: need n >= 2, p >= 1, ldc, ldx >= p, counts and x_out or the planes");
   if ((const void*)counts == (const void*)x_out && ldc != ldx)
     return fail(h, GMGM_E_ARG, "gmgm_preprocess: in-place needs ldx == ldc");
   if ((xt_hi == nullptr) != (xt_lo == nullptr))

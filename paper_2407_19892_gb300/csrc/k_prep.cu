@@ -57,7 +57,7 @@ __global__ void centre_split_kernel(const float* c, int64_t n, int64_t p,
     float v = 0.f;
     if (row < n && col < p) {
       v = log1pf(c[row * ldc + col]) - mean;
-      x[row * ldx + col] = v;
+      if (x) x[row * ldx + col] = v;  // (null: only the planes are wanted)
     }
     tile[rr][tx] = v;
   }

@@ -38,6 +38,10 @@ def test_preprocess_matches_oracle(g, cuda_dev, n, p):
     assert xt.shape == (p, ld_t) and ld_t % 64 == 0
     np.testing.assert_allclose(xt[:, :n], x.cpu().numpy().T, atol=1e-4 * max(1.0, np.abs(ref).max()))
     assert np.all(xt[:, n:] == 0)
+    # planes only (no FP32 X written): the same planes, bit for bit
+    x2, hi2, lo2, ld2 = g.preprocess(counts.to(cuda_dev), split=True, x_out=False)
+    assert x2 is None and ld2 == ld_t
+    assert torch.equal(hi2, hi) and torch.equal(lo2, lo)
 
 
 # ---- Gram ------------------------------------------------------------------
