@@ -7,7 +7,8 @@
 //   2. multisection with division-free double-float Sturm counts for the
 //      wanted eigenvalues of T (sixteen lanes per eigenvalue);
 //   3. inverse iteration on T - lambda I (tridiagonal LU with partial
-//      pivoting, one thread per eigenvalue, double-float), then modified
+//      pivoting, one thread per eigenvalue, double-float, work arrays in
+//      shared memory when they fit), then modified
 //      Gram-Schmidt inside clusters of nearly equal eigenvalues;
 //   4. back-transformation Z <- Q Z in compact WY blocks of 32 reflectors
 //      (one cooperative kernel over every SM, one grid barrier per block);
@@ -409,50 +410,29 @@ __device__ __forceinline__ float hash_unit_f(uint32_t a, uint32_t b) {
   return __fmaf_rn(__uint2float_rn(x), 0x1p-31f, -1.f);
 }
 
-// Inverse iteration: thread t (eigenvalue lam[t]) solves (T - lam I) z = y
-// kInvIters times from a pseudo-random start, in double-float on c T (c a
-// power of two with ||c T|| about 1; the block's copy in shared memory):
-// each step's quotient and updates are a few dozen FP32 operations instead
-// of an FP64 division on a pipe that issues about one lane per clock.  Work
-// arrays are interleaved [i][t] (stride B) so that a warp's accesses
-// coalesce; z ends, normalised, in Z[i*B + t] as FP64 (the same 8 bytes
-// that held the double-float iterate).
-__global__ void inverse_iter_kernel(const double* __restrict__ dv, const double* __restrict__ ev, int n,
-                                    const double* __restrict__ lam, int cnt, int B,
-                                    const double* __restrict__ info, dfl* __restrict__ u0, dfl* __restrict__ u1,
-                                    dfl* __restrict__ u2, double* __restrict__ Zd, int seed_base) {
-  extern __shared__ dfl inv_sm[];
-  dfl* sd = inv_sm;      // c T's diagonal
-  dfl* se = inv_sm + n;  // c T's off-diagonal (0 past the end)
-  int ce = 0;
-  {
-    const double tn = info[3];
-    if (tn > 0.0 && isfinite(tn)) frexp(tn, &ce);
-  }
-  const double cs = ldexp(1.0, -ce);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    sd[i] = df_from(dv[i] * cs);
-    se[i] = i + 1 < n ? df_from(ev[i] * cs) : df_zero();
-  }
-  __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  dfl* Z = reinterpret_cast<dfl*>(Zd);
-  const dfl nlm = df_from(-lam[t] * cs);
-  const float tiny = 0x1p-52f * float(fmax(info[3], DBL_MIN) * cs);
-  for (int i = 0; i < n; ++i) Z[int64_t(i) * B + t] = dfl{hash_unit_f(uint32_t(seed_base + t), uint32_t(i)), 0.f};
+// Inverse iteration for one eigenvalue: solves (T - lam I) z = y kInvIters
+// times from a pseudo-random start, in double-float on c T (c a power of two
+// with ||c T|| about 1; sd, se its diagonal and off-diagonal): each step's
+// quotient and updates are a few dozen FP32 operations instead of an FP64
+// division on a pipe that issues about one lane per clock.  Entry i of the
+// work arrays Z, u0, u1, u2 sits at [i * st]; z ends, normalised, in
+// out[i * ost] as FP64.
+__device__ __forceinline__ void inverse_iter_one(const dfl* sd, const dfl* se, int n, dfl nlm, float tiny, uint32_t seed,
+                                                 dfl* Z, dfl* u0, dfl* u1, dfl* u2, int64_t st, double* out,
+                                                 int64_t ost) {
+  for (int i = 0; i < n; ++i) Z[int64_t(i) * st] = dfl{hash_unit_f(seed, uint32_t(i)), 0.f};
   for (int iter = 0; iter < kInvIters; ++iter) {
     // factor with partial pivoting while applying L^-1 to the right-hand side
     dfl a = df_add(sd[0], nlm), b = se[0];
-    dfl y = Z[t];  // current y_i (after elimination of previous rows)
+    dfl y = Z[0];  // current y_i (after elimination of previous rows)
     for (int i = 0; i + 1 < n; ++i) {
       const dfl c = se[i];
       const dfl na = df_add(sd[i + 1], nlm);
       const dfl nb = se[i + 1 < n ? i + 1 : i];
       const dfl nbv = i + 2 < n ? nb : df_zero();
-      const dfl ynext = Z[int64_t(i + 1) * B + t];
+      const dfl ynext = Z[int64_t(i + 1) * st];
       dfl yi, ynew;
-      const int64_t o = int64_t(i) * B + t;
+      const int64_t o = int64_t(i) * st;
       if (fabsf(a.h) >= fabsf(c.h)) {
         const dfl piv = fabsf(a.h) < tiny ? dfl{a.h < 0.f ? -tiny : tiny, 0.f} : a;
         const dfl nl = df_neg(df_div(c, piv));
@@ -479,10 +459,10 @@ __global__ void inverse_iter_kernel(const double* __restrict__ dv, const double*
     const dfl last = fabsf(a.h) < tiny ? dfl{a.h < 0.f ? -tiny : tiny, 0.f} : a;
     // back substitution, tracking the largest magnitude for scaling
     dfl z2 = df_zero(), z1 = df_div(y, last);
-    Z[int64_t(n - 1) * B + t] = z1;
+    Z[int64_t(n - 1) * st] = z1;
     float zmax = fabsf(z1.h);
     for (int i = n - 2; i >= 0; --i) {
-      const int64_t o = int64_t(i) * B + t;
+      const int64_t o = int64_t(i) * st;
       const dfl zi = df_div(df_sub2(Z[o], u1[o], z1, u2[o], z2), u0[o]);
       Z[o] = zi;
       z2 = z1;
@@ -493,21 +473,74 @@ __global__ void inverse_iter_kernel(const double* __restrict__ dv, const double*
     // write FP64
     const dfl sc{1.f / fmaxf(zmax, FLT_MIN), 0.f};
     if (iter + 1 < kInvIters) {
-      for (int i = 0; i < n; ++i) Z[int64_t(i) * B + t] = df_mul(Z[int64_t(i) * B + t], sc);
+      for (int i = 0; i < n; ++i) Z[int64_t(i) * st] = df_mul(Z[int64_t(i) * st], sc);
     } else {
       dfl nn = df_zero();
       for (int i = 0; i < n; ++i) {
-        const dfl zi = df_mul(Z[int64_t(i) * B + t], sc);
+        const dfl zi = df_mul(Z[int64_t(i) * st], sc);
         nn = df_fma(nn, zi, zi);
       }
       const dfl s2 = df_div(sc, df_sqrt(nn));
-      for (int i = 0; i < n; ++i) {
-        const int64_t o = int64_t(i) * B + t;
-        const dfl zi = df_mul(Z[o], s2);
-        Zd[o] = df_val(zi);
-      }
+      for (int i = 0; i < n; ++i) out[int64_t(i) * ost] = df_val(df_mul(Z[int64_t(i) * st], s2));
     }
   }
+}
+
+// c T in double-float into shared memory (sd, se; se 0 past the end), and
+// the power-of-two scale c.
+__device__ __forceinline__ double load_scaled_tri(const double* __restrict__ dv, const double* __restrict__ ev, int n,
+                                                  const double* __restrict__ info, dfl* sd, dfl* se) {
+  int ce = 0;
+  {
+    const double tn = info[3];
+    if (tn > 0.0 && isfinite(tn)) frexp(tn, &ce);
+  }
+  const double cs = ldexp(1.0, -ce);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = df_from(dv[i] * cs);
+    se[i] = i + 1 < n ? df_from(ev[i] * cs) : df_zero();
+  }
+  __syncthreads();
+  return cs;
+}
+
+// Inverse iteration, one thread per eigenvalue lam[t], work arrays in global
+// memory interleaved [i][t] (stride B) so that a warp's accesses coalesce;
+// z ends in Zd[i*B + t] (the same 8 bytes that held the double-float
+// iterate).  For tridiagonals too long for the shared-memory form below.
+__global__ void inverse_iter_kernel(const double* __restrict__ dv, const double* __restrict__ ev, int n,
+                                    const double* __restrict__ lam, int cnt, int B,
+                                    const double* __restrict__ info, dfl* __restrict__ u0, dfl* __restrict__ u1,
+                                    dfl* __restrict__ u2, double* __restrict__ Zd, int seed_base) {
+  extern __shared__ dfl inv_sm[];
+  dfl* sd = inv_sm;
+  dfl* se = inv_sm + n;
+  const double cs = load_scaled_tri(dv, ev, n, info, sd, se);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const dfl nlm = df_from(-lam[t] * cs);
+  const float tiny = 0x1p-52f * float(fmax(info[3], DBL_MIN) * cs);
+  inverse_iter_one(sd, se, n, nlm, tiny, uint32_t(seed_base + t), reinterpret_cast<dfl*>(Zd) + t, u0 + t, u1 + t,
+                   u2 + t, B, Zd + t, B);
+}
+
+// The same solves with each thread's work arrays in shared memory (4n
+// double-float per eigenvalue after the 2n of c T): every step of the two
+// sequential sweeps reads and writes shared memory instead of waiting on
+// an L2 round trip.  Output as inverse_iter_kernel (Zd[i*B + t], FP64).
+__global__ void inverse_iter_smem_kernel(const double* __restrict__ dv, const double* __restrict__ ev, int n,
+                                         const double* __restrict__ lam, int cnt, int B,
+                                         const double* __restrict__ info, double* __restrict__ Zd, int seed_base) {
+  extern __shared__ dfl inv_sm[];
+  dfl* sd = inv_sm;
+  dfl* se = inv_sm + n;
+  const double cs = load_scaled_tri(dv, ev, n, info, sd, se);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  dfl* wk = inv_sm + 2 * n + int64_t(threadIdx.x) * 4 * n;  // Z, u0, u1, u2 of this thread
+  const dfl nlm = df_from(-lam[t] * cs);
+  const float tiny = 0x1p-52f * float(fmax(info[3], DBL_MIN) * cs);
+  inverse_iter_one(sd, se, n, nlm, tiny, uint32_t(seed_base + t), wk, wk + n, wk + 2 * n, wk + 3 * n, 1, Zd + t, B);
 }
 
 // Z interleaved [i][t] (stride B) -> Zc eigenvector-major [t][i].
@@ -843,14 +876,29 @@ cudaError_t launch_eig(gmgm_handle* h, int64_t d64, const double* S, int64_t lds
     }
     const int B = std::min(nvec, kInvBatch);
     const size_t ismem = size_t(2) * n * sizeof(dfl);
-    if ((e = cudaFuncSetAttribute(inverse_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem))) !=
-        cudaSuccess)
+    // eigenvalues per block with the work arrays in shared memory (0: too long)
+    int smem_optin = 0;
+    if ((e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device)) != cudaSuccess)
       return e;
+    const size_t per_vec = size_t(4) * n * sizeof(dfl);
+    const int vpb = size_t(smem_optin) > ismem ? int(std::min<size_t>(32, (size_t(smem_optin) - ismem) / per_vec)) : 0;
+    if (vpb > 0) {
+      if ((e = cudaFuncSetAttribute(inverse_iter_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(ismem + vpb * per_vec))) != cudaSuccess)
+        return e;
+    } else if ((e = cudaFuncSetAttribute(inverse_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(ismem))) != cudaSuccess) {
+      return e;
+    }
     for (int t0 = 0; t0 < nvec; t0 += B) {
       const int cnt = std::min(B, nvec - t0);
-      inverse_iter_kernel<<<unsigned((cnt + 31) / 32), 32, ismem, st>>>(
-          s.dv, s.ev, n, lamv + t0, cnt, B, s.info, reinterpret_cast<dfl*>(s.u0), reinterpret_cast<dfl*>(s.u1),
-          reinterpret_cast<dfl*>(s.u2), s.Z, t0);
+      if (vpb > 0)
+        inverse_iter_smem_kernel<<<unsigned((cnt + vpb - 1) / vpb), unsigned(vpb), ismem + vpb * per_vec, st>>>(
+            s.dv, s.ev, n, lamv + t0, cnt, B, s.info, s.Z, t0);
+      else
+        inverse_iter_kernel<<<unsigned((cnt + 31) / 32), 32, ismem, st>>>(
+            s.dv, s.ev, n, lamv + t0, cnt, B, s.info, reinterpret_cast<dfl*>(s.u0), reinterpret_cast<dfl*>(s.u1),
+            reinterpret_cast<dfl*>(s.u2), s.Z, t0);
       dim3 tb(32, 8), tg(unsigned((cnt + 31) / 32), unsigned((n + 31) / 32));
       transpose_kernel<<<tg, tb, 0, st>>>(s.Z, n, cnt, B, s.Zc, t0);
       launches += 2;
