@@ -55,43 +55,57 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return red[32];
 }
 
-// Spin limit for grid barriers: ~2^26 polls (a few seconds at most).
-constexpr long long kBarrierSpinLimit = 1ll << 26;
+// A grid barrier gives up after this long.
+constexpr unsigned long long kBarrierWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long device_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Grid barrier for a cooperative launch (all CTAs resident), on a counter
 // of arrivals that only grows during the launch: bar[0] = arrivals (zeroed
 // before the launch), bar[2] = abort flag.  `epoch` counts the barriers this
 // CTA has passed (every CTA passes the same ones), so barrier e completes
-// when bar[0] reaches (e + 1) * nblocks: one atomic per CTA and no reset or
-// generation word on the critical path.  Every wait is bounded: on timeout
-// the TIMEOUT status bit and the abort flag are set and the function
-// returns false; callers then leave the kernel.  Once aborted, every later
-// call returns false immediately.
+// when bar[0] reaches (e + 1) * nblocks.  One CTA-wide sync, then thread 0
+// arrives with one acquire-release atomic (the CTA's writes, ordered before
+// it by the sync, become visible to every CTA that acquires the count) and
+// polls the count with acquire loads; no other global access sits on the
+// path.  Every wait is bounded: after kBarrierWaitNs, or once another CTA
+// has raised the abort flag (read every 64 polls), the TIMEOUT status bit
+// and the abort flag are set and the function returns false; callers then
+// leave the kernel, and any CTA still waiting at a later barrier sees the
+// flag and leaves too.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& epoch, int* status) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vb = bar;
-    int ok = vb[2] == 0u;
-    if (ok) {
-      const unsigned target = (epoch + 1u) * nblocks;
-      __threadfence();  // this CTA's writes (ordered before by the CTA barrier) before the arrival
-      const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
-      if (arrived != target) {
-        long long spins = 0;
-        while (static_cast<int>(vb[0] - target) < 0) {
-          if (vb[2] != 0u || ++spins > kBarrierSpinLimit) {
+    int ok = 1;
+    const unsigned target = (epoch + 1u) * nblocks;
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    if (old + 1u != target) {
+      unsigned spins = 0;
+      unsigned long long t0 = 0;
+      for (;;) {
+        unsigned cur;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
+        if (static_cast<int>(cur - target) >= 0) break;
+        if ((++spins & 63u) == 0u) {
+          const unsigned long long t = device_ns();
+          if (t0 == 0) {
+            t0 = t;
+          } else if (reinterpret_cast<volatile unsigned*>(bar)[2] != 0u || t - t0 > kBarrierWaitNs) {
             ok = 0;
             break;
           }
-          __nanosleep(32);
-        }
-        if (!ok) {
-          atomicExch(&bar[2], 1u);
-          set_status(status, GMGM_DEV_TIMEOUT);
         }
       }
-      __threadfence();
+      if (!ok) {
+        atomicExch(&bar[2], 1u);
+        set_status(status, GMGM_DEV_TIMEOUT);
+      }
     }
     ok_s = ok;
   }

@@ -102,6 +102,23 @@ __device__ __forceinline__ bool reflector_scalars(dfl x0, dfl tail, dfl& tau, df
   return true;
 }
 
+// acc += a b with the sum kept as an unnormalised pair (s, t): s the exact
+// running sum of the high products (TwoSum), t the FP32 sum of every
+// low-order term; renormalised once at the end (df_renorm(s, t)).  Six
+// FP32 operations fewer than df_fma per term; with at most a few dozen
+// terms per pair t stays within a few ulp(s), so the FP32 rounding of t is
+// far below the double-float unit.
+__device__ __forceinline__ void df_fma_acc(float& s, float& t, dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  float s2, t2;
+  two_sum(s, p, s2, t2);
+  s = s2;
+  t = __fadd_rn(t, __fadd_rn(t2, e));
+}
+
 // Tridiagonalisation with one grid barrier per reflector: the rank-2 update
 // of step k and the mat-vec of step k+1 share one pass over the trailing
 // matrix.  Row k+1 of the updated matrix (which defines reflector k+1) is
@@ -232,9 +249,9 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
       float2* row = reinterpret_cast<float2*>(A) + int64_t(k + 1 + t) * n + k + 2;
       const dfl vi = vb[t], wi = w[t];
       const int mm = m - 1;
-      dfl acc[kBatch];
+      float sh[kBatch], sl[kBatch];  // unnormalised partial sums of (row . u)
 #pragma unroll
-      for (int q = 0; q < kBatch; ++q) acc[q] = df_zero();
+      for (int q = 0; q < kBatch; ++q) sh[q] = sl[q] = 0.f;
       // kBatch independent L2 loads per lane; the next batch's are issued
       // before this batch's update, so two batches are in flight
       float2 a[kBatch];
@@ -256,15 +273,16 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(dfl* A, int n, con
               x = df_sub2(x, vi, w[1 + jj], wi, vb[1 + jj]);
               row[jj] = make_float2(x.h, x.l);
             }
-            acc[q] = df_fma(acc[q], x, uu[1 + jj]);
+            df_fma_acc(sh[q], sl[q], x, uu[1 + jj]);
           }
         }
 #pragma unroll
         for (int q = 0; q < kBatch; ++q) a[q] = nx[q];
       }
+      dfl acc = df_renorm(sh[0], sl[0]);
 #pragma unroll
-      for (int q = 1; q < kBatch; ++q) acc[0] = df_add(acc[0], acc[q]);
-      const dfl s = df_warp_sum(acc[0]);
+      for (int q = 1; q < kBatch; ++q) acc = df_add(acc, df_renorm(sh[q], sl[q]));
+      const dfl s = df_warp_sum(acc);
       if (lane == 0 && more) Pn[it] = df_mul(tnd, s);
     }
     // the next reflector is ub + 1; the current one's buffer takes row k+2
